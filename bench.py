@@ -1,0 +1,350 @@
+#!/usr/bin/env python3
+"""Benchmark of the local CSR SpMM C = A*B on one GB300 (replicas on N GPUs).
+
+Workload (the power-law FP32 SpMM): A is an R-MAT graph of scale 22
+(4,194,304 rows and columns), edge factor 16, (a,b,c,d) = (0.57,0.19,0.19,0.05),
+duplicates merged, self-loops kept, values uniform (0,1] in FP32; B is
+4,194,304 x 128 FP32 N(0,1); a 16 x 4 tile grid (16 C row blocks x 4 column
+blocks of 32) is pulled by the persistent work-stealing kernel.  Inputs are
+synthetic and seeded, and larger than L2.
+
+One step = one spmm_csr call (counter reset + one persistent kernel launch).
+`value` is GFLOP/s = 2*nnz*N / step time over all ranks (N>1 runs independent
+replicas: the path has no exchange step, so there is no collective).
+
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SpMM GFLOP/s (2·nnz·N) and % HBM roofline; BF16 vs FP32 at stated error"
+WORKLOAD = "rmat-s22-ef16-n128-fp32-grid16x4"
+FALLBACK_HBM_GBS = 6800.0
+PROFILE = os.path.join(ROOT, "profiles", "spmm_csr_persistent_rmat_s22_n128.md")
+KERNEL_SOURCES = ["common.cuh", "spmm_kernel.cuh", "spmm_launch_impl.cuh", "spmm_f32.cu",
+                  "plan.cu"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=int, default=22, help="R-MAT scale (22 = the workload)")
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--grid", default="16x4")
+    ap.add_argument("--chunk", type=int, default=0)
+    ap.add_argument("--warps", type=int, default=0)
+    ap.add_argument("--order", type=int, default=0)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2311_18141_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic(src_hash: str):
+    """dram read+write bytes per launch from the committed ncu summary, if it was
+    taken on the current kernel source."""
+    try:
+        text = open(PROFILE).read()
+    except OSError:
+        return None
+    m_hash = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    m_traffic = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    if not m_hash or not m_traffic or m_hash.group(1) != src_hash:
+        return None
+    return float(m_traffic.group(1))
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.out = []
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            time.sleep(0.6)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        self.out = [l.split(",") for l in out.strip().splitlines() if l.count(",") >= 8]
+
+    def summary(self):
+        if not self.out:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = sorted(float(r[1]) for r in self.out)
+        mx = max(float(r[2]) for r in self.out)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.out for k in range(4)
+                          if r[5 + k].strip().lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(sm)}
+
+
+def make_workload(scale, n, device):
+    from paper_2311_18141_gb300 import inputs
+    A = inputs.rmat_csr(scale, 16, 0.57, 0.19, 0.19, seed=1, device=device, values="pos")
+    B = inputs.dense_normal(A.K, n, seed=2, device=device)
+    return A, B
+
+
+def min_bytes(M, K, N, nnz, w_val=4, w_b=4, w_c=4):
+    """Local SpMM bytes of Section 4 at p = 1: CSR (rowptr, colind, vals), B, C once."""
+    return 4 * (M + 1) + nnz * (4 + w_val) + K * N * w_b + M * N * w_c
+
+
+def cpu_oracle_sample(A, B, seconds: float):
+    """Time the FP64 oracle on a stride sample of rows, growing it until about
+    `seconds` of CPU work; returns (GFLOP/s, cores, description)."""
+    import numpy as np
+    import oracle
+    cores = len(os.sched_getaffinity(0))
+    oracle.set_threads(cores)
+    rp = A.rowptr.cpu().numpy()
+    ci = A.colind.cpu().numpy()
+    v = A.vals.cpu().numpy()
+    Bh = B.cpu().numpy()
+    N = Bh.shape[1]
+    lens = np.diff(rp.astype(np.int64))
+    stride = 4096
+    total_t, total_flops, rows_done = 0.0, 0.0, 0
+    while stride >= 1:
+        rows = np.arange(0, A.M, stride, dtype=np.int64)
+        t = time.perf_counter()
+        oracle.spmm_rows(rp, ci, v, Bh, rows)
+        dt = time.perf_counter() - t
+        total_t, total_flops, rows_done = dt, 2.0 * float(lens[rows].sum()) * N, rows.size
+        if dt >= seconds / 4 or stride == 1:
+            break
+        stride //= 4
+    desc = (f"every {stride}-th row of the workload ({rows_done} rows, "
+            f"{total_flops / 2 / N:.0f} nnz), N={N}, FP64 oracle, {total_t:.2f} s")
+    return total_flops / total_t / 1e9, oracle.get_threads(), desc, total_t
+
+
+def run_reference(args):
+    """The FP64 oracle on the host cores (rank 0 only)."""
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    A, B = make_workload(args.scale, args.n, "cuda" if torch.cuda.is_available() else "cpu")
+    vals = []
+    per_step = max(0.5, min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_oracle_sample(A, B, per_step)
+    desc = cores = None
+    for _ in range(args.steps):
+        g, cores, desc, _ = cpu_oracle_sample(A, B, per_step)
+        vals.append(g)
+    value = sum(vals) / len(vals)
+    flops_step = 2.0 * A.nnz * args.n
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": flops_step / (value * 1e9) * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "M": A.M, "K": A.K, "N": args.n, "nnz": A.nnz},
+        "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2311_18141_gb300 import binding
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    binding.load_library()
+    TR, TC = (int(x) for x in args.grid.split("x"))
+    A, B = make_workload(args.scale, args.n, dev)
+    M, K, N, nnz = A.M, A.K, args.n, A.nnz
+    C = torch.empty(M, N, device=dev)
+    tun = binding.make_tuning(chunk_items=args.chunk, warps_per_cta=args.warps,
+                              tile_order=args.order)
+    plan = binding.Plan(A.rowptr, M, K, nnz, N, TR, TC, tuning=tun)
+    ws = binding.workspace(plan.workspace_bytes, dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        binding.spmm_csr(A.rowptr, A.colind, A.vals, B, C, M, K, N, nnz, plan=plan, ws=ws,
+                         stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    assert binding.spmm_get_device_status(ws) == 0
+
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        gpu_id = str(local)
+    sampler = ClockSampler(gpu_id)
+    sampler.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    for k in range(args.steps):
+        step()
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    sampler.stop()
+    total_ms = ev[0].elapsed_time(ev[-1])
+    per_launch = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_step = total_ms / args.steps
+    flops = 2.0 * nnz * N
+    value = flops * world / (ms_step * 1e-3) / 1e9
+
+    # roofline of the dominant kernel (one launch per step)
+    peak, peak_kind = measured_peaks()
+    algo_bytes = min_bytes(M, K, N, nnz)
+    launch_ms = sum(per_launch) / len(per_launch)
+    achieved = algo_bytes / (launch_ms * 1e-3) / 1e9
+    src_hash = kernel_source_hash()
+    traffic = stored_traffic(src_hash)
+
+    # end-to-end through the public API with host buffers
+    e2e = None
+    if rank == 0 or world > 1:
+        rp_h = A.rowptr.cpu().pin_memory()
+        ci_h = A.colind.cpu().pin_memory()
+        v_h = A.vals.cpu().pin_memory()
+        B_h = B.cpu().pin_memory()
+        C_h = torch.empty(M, N).pin_memory()
+        rp_d, ci_d, v_d = torch.empty_like(A.rowptr), torch.empty_like(A.colind), torch.empty_like(A.vals)
+        B_d = torch.empty_like(B)
+        h2d = sum(t.numel() * t.element_size() for t in (rp_h, ci_h, v_h, B_h))
+        d2h = C_h.numel() * C_h.element_size()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n_e2e = max(1, args.e2e_steps)
+        e0.record(stream)
+        for _ in range(n_e2e):
+            rp_d.copy_(rp_h, non_blocking=True)
+            ci_d.copy_(ci_h, non_blocking=True)
+            v_d.copy_(v_h, non_blocking=True)
+            B_d.copy_(B_h, non_blocking=True)
+            binding.spmm_csr(rp_d, ci_d, v_d, B_d, C, M, K, N, nnz, plan=plan, ws=ws, stream=stream)
+            C_h.copy_(C, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = e0.elapsed_time(e1) / n_e2e
+        e2e = {"value": flops * world / (e2e_ms * 1e-3) / 1e9, "unit": "GFLOP/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+               "steps": n_e2e}
+        del rp_h, ci_h, v_h, B_h, C_h, B_d
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        g, cores, desc, _ = cpu_oracle_sample(A, B, args.cpu_seconds)
+        cpu = {"value": g, "unit": "GFLOP/s", "cores": cores, "kind": "oracle", "sample": desc}
+
+    chunks, units = plan.units()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD if (args.scale, N, args.grid) == (22, 128, "16x4")
+                       else f"rmat-s{args.scale}-ef16-n{N}-fp32-grid{args.grid}",
+                       "M": M, "K": K, "N": N, "nnz": nnz, "tile_grid": args.grid,
+                       "chunks": chunks, "work_units": units,
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 gpu",
+                       "l2": "inputs larger than L2 (A+B+C = %.2f GB per step)" % (algo_bytes / 1e9)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": f"{peak_kind} (copy bandwidth)",
+                         "algorithmic_bytes_per_launch": algo_bytes,
+                         "kernel": "spmm_csr_persistent<TagF32,8,1>",
+                         "launch_ms": launch_ms, "kernel_source_sha256_16": src_hash},
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": args.steps,
+            "clocks": sampler.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,215 @@
+/*
+ * spmm_gb300.h -- C ABI of the GB300 CSR sparse-times-dense product library.
+ *
+ * The library computes the local tile product of Brock, Bulu\c{c} and Yelick,
+ * "RDMA-Based Algorithms for Sparse Matrix Multiplication on GPUs" (ICS'24):
+ * C_ij = C_ij + sum_k A_ik B_kj (Section 2.1), where A is a CSR matrix and B, C
+ * are dense.  The paper's distributed, asynchronous, work-stealing schedule
+ * (Sections 3.2-3.4, Algorithms 2 and 3) is re-expressed inside one GPU: the
+ * C-row-block x B-column-block tiles of a 2D tile grid are work queues that a
+ * persistent kernel's warps reserve from with atomic fetch-and-add, and a warp
+ * whose own tile is empty steals from other tiles, same tile row first.
+ *
+ * Conventions for every entry point:
+ *   - Pointers marked "device" are CUDA device (or managed) pointers owned by
+ *     the caller; pointers marked "host" are ordinary host pointers.  The
+ *     library never frees caller memory and never keeps a caller pointer past
+ *     the call, except that a plan keeps nothing but its own device arrays.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *     default stream.  All device work is enqueued asynchronously on it; the
+ *     calls do not synchronise unless documented.
+ *   - Dense matrices are row-major with a leading dimension in ELEMENTS
+ *     (ldb >= N, ldc >= N).  Vector paths need B, C, ldb*elem_size and
+ *     ldc*4 to be 16-byte aligned and N a multiple of the elements in 16 bytes
+ *     of B's type (4 for F32, 8 for F16/BF16, 16 for E4M3); otherwise the call
+ *     returns SPMM_ERR_MISALIGNED and enqueues nothing.
+ *   - Indices are int32; nnz < 2^31.  CSR rows may be in any column order and
+ *     may repeat a column (repeats are summed); rowptr must be non-decreasing
+ *     with rowptr[0] = 0 and rowptr[M] = nnz, and every column index must lie
+ *     in [0, K).  Compute calls trust this; spmm_csr_validate checks it.
+ *   - Every entry point returns an int status: SPMM_OK (0) or a negative code
+ *     below.  No entry point exits, traps or throws.  Errors found by device
+ *     code are written to a status word in the caller's workspace and read
+ *     with spmm_get_device_status.
+ *   - The hot calls (spmm_csr with a plan, spmm_sddmm_csr with a plan,
+ *     spmm_csr_batched) allocate no memory: all scratch comes from the
+ *     caller's workspace.  Plan creation allocates (cudaMalloc) and is meant
+ *     to happen once per sparsity pattern.
+ */
+#ifndef SPMM_GB300_H
+#define SPMM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define SPMM_OK 0
+#define SPMM_ERR_INVALID_ARG (-1)   /* null pointer, negative size, bad enum    */
+#define SPMM_ERR_MISALIGNED (-2)    /* vector-path alignment rule broken         */
+#define SPMM_ERR_UNSUPPORTED (-3)   /* dtype or width combination not built      */
+#define SPMM_ERR_CUDA (-4)          /* a CUDA runtime call failed                */
+#define SPMM_ERR_BAD_CSR (-5)       /* validator found a malformed CSR           */
+#define SPMM_ERR_TIMEOUT (-6)       /* a bounded device wait ran out             */
+#define SPMM_ERR_WORKSPACE (-7)     /* workspace missing or too small            */
+#define SPMM_ERR_PLAN_MISMATCH (-8) /* plan built for another shape or grid      */
+#define SPMM_ERR_INTERNAL (-9)      /* device sanity check on the plan failed    */
+
+/* ---- element types ---- */
+#define SPMM_F32 0   /* IEEE binary32                                   */
+#define SPMM_F16 1   /* IEEE binary16                                   */
+#define SPMM_BF16 2  /* bfloat16                                        */
+#define SPMM_E4M3 3  /* OCP FP8 E4M3 (finite variant, max 448)          */
+
+typedef struct spmm_plan_s* spmm_plan;
+
+/* Tuning knobs; a zero field means "library default".  Host struct. */
+typedef struct spmm_tuning {
+    int32_t chunk_items;   /* merge-path items (rows + nonzeros) per work unit        */
+    int32_t warps_per_cta; /* 4 or 8                                                  */
+    int32_t ctas_per_sm;   /* persistent CTAs per SM; 0 = as many as fit              */
+    int32_t tile_order;    /* 0: steal along the tile row first, 1: along the column   */
+    int32_t reserved[4];
+} spmm_tuning;
+
+/* Human-readable name of a status code (static storage). */
+const char* spmm_status_string(int status);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int spmm_version(void);
+
+/*
+ * spmm_plan_create -- cut A into work units for a tile_rows x tile_cols grid.
+ *   Section 2.1 tiles C into a grid of row blocks x column blocks; Section 3.4
+ *   (Algorithm 3) reserves work inside a tile with fetch-and-add.  The plan
+ *   splits each C row block's merge path (its rows interleaved with its
+ *   nonzeros) into equal runs of `chunk_items` items; every (chunk, column
+ *   block) pair is one work unit, so a heavy row is shared by several units.
+ *   A_rowptr  device int32[M+1], read on `stream` during this call.
+ *   M, K, nnz, N  problem shape (N = columns of B and C).
+ *   tile_rows, tile_cols  grid shape, 1 <= tile_rows <= 65536,
+ *                 1 <= tile_cols <= N/vector width.  Column blocks are ceil(N /
+ *                 tile_cols) rounded up to whole 16-byte vectors; the last one
+ *                 may be narrower.
+ *   tuning    host, nullable.
+ *   On success *plan owns device memory; the plan arrays are complete once
+ *   `stream` reaches this point.  Free with spmm_plan_destroy.
+ */
+int spmm_plan_create(spmm_plan* plan, const int32_t* A_rowptr, int64_t M, int64_t K,
+                     int64_t nnz, int64_t N, int32_t tile_rows, int32_t tile_cols,
+                     const spmm_tuning* tuning, void* stream);
+
+/* Release a plan (synchronises the device first).  NULL is accepted. */
+int spmm_plan_destroy(spmm_plan plan);
+
+/* Bytes of per-call scratch a call with this plan needs (host out-param). */
+int spmm_plan_workspace_size(spmm_plan plan, size_t* bytes);
+
+/* Number of work units (chunks x column blocks) of a plan, for reporting. */
+int spmm_plan_units(spmm_plan plan, int64_t* chunks, int64_t* units);
+
+/* Bytes of workspace a spmm_csr call with plan == NULL needs: the plan arrays
+ * plus the per-call scratch.  Such calls use the default tuning; `tuning` is
+ * reserved and should be NULL. */
+int spmm_csr_workspace_size(int64_t M, int64_t nnz, int64_t N, int32_t tile_rows,
+                            int32_t tile_cols, const spmm_tuning* tuning, size_t* bytes);
+
+/*
+ * spmm_csr -- C = beta*C + diag(A_row_scale) * A * (diag(B_row_scale) * B).
+ *   This is the local product C_ij = C_ij + sum_k A_ik B_kj of Section 2.1
+ *   (the "local_c += local_a*local_b" step of Algorithm 2) computed for all
+ *   tiles of the grid by one persistent launch; beta = 1 is the paper's
+ *   accumulate, beta = 0 overwrites (C is then never read, NaNs included).
+ *   A_rowptr, A_colind  device int32 CSR arrays.
+ *   A_vals     device, nnz values of type a_dtype (F32, F16, BF16 or E4M3).
+ *   A_row_scale device float[M] or NULL: row r of A is multiplied by it.
+ *   B          device, K x N of type b_dtype (F32, F16, BF16 or E4M3), row
+ *              stride ldb elements.
+ *   B_row_scale device float[K] or NULL: row k of B is multiplied by it.
+ *   C          device float, M x N, row stride ldc.  Accumulation is FP32.
+ *   tile_rows, tile_cols  must equal the plan's (or be 0 to take the plan's).
+ *   plan       from spmm_plan_create for the same rowptr/shape, or NULL to build
+ *              the plan inside `workspace` on every call.
+ *   workspace  device scratch of at least spmm_plan_workspace_size (plan) or
+ *              spmm_csr_workspace_size (NULL plan) bytes, 256-byte aligned.
+ *              Calls that share a workspace must not overlap on the GPU.
+ *   Rows that the plan splits between work units are summed through the
+ *   workspace in a fixed order by whichever unit finishes last, so results
+ *   are bitwise reproducible run to run for a given plan and launch shape.
+ */
+int spmm_csr(const int32_t* A_rowptr, const int32_t* A_colind, const void* A_vals,
+             int32_t a_dtype, const float* A_row_scale, const void* B, int32_t b_dtype,
+             const float* B_row_scale, int64_t ldb, float* C, int64_t ldc, int64_t M,
+             int64_t K, int64_t N, int64_t nnz, int32_t tile_rows, int32_t tile_cols,
+             float beta, spmm_plan plan, void* workspace, size_t workspace_bytes,
+             void* stream);
+
+/*
+ * spmm_csr_validate -- check the CSR invariants listed above on the device.
+ *   Writes SPMM_OK or SPMM_ERR_BAD_CSR into the workspace status word (the
+ *   first 64 bytes of `workspace`, which must hold at least 64 bytes); read it
+ *   with spmm_get_device_status.  Never faults on a bad CSR: it reads only
+ *   rowptr[0..M] and colind[0..nnz).
+ */
+int spmm_csr_validate(const int32_t* A_rowptr, const int32_t* A_colind, int64_t M, int64_t K,
+                      int64_t nnz, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Synchronise `stream`, then copy the device status word of `workspace` into
+ * *status (host) and clear it. */
+int spmm_get_device_status(void* workspace, int32_t* status, void* stream);
+
+/*
+ * spmm_csr_transpose -- CSR of A (M x K) -> CSR of A^T (K x M), i.e. A's CSC.
+ *   Needed by the backward pass dB = A^T dC.  Built on the device by a stable
+ *   least-significant-digit radix sort of the nonzeros by column, so each
+ *   column lists its rows in increasing order and the output is identical run
+ *   to run.
+ *   out_colptr device int32[K+1]; out_rowind device int32[nnz];
+ *   out_vals   device, nnz elements of val_dtype (may be NULL);
+ *   out_perm   device int32[nnz] or NULL: CSR position of each CSC entry, so
+ *              values can be re-gathered later without a new sort.
+ *   workspace  at least spmm_csr_transpose_workspace_size bytes.
+ */
+int spmm_csr_transpose_workspace_size(int64_t M, int64_t K, int64_t nnz, size_t* bytes);
+int spmm_csr_transpose(const int32_t* A_rowptr, const int32_t* A_colind, const void* A_vals,
+                       int32_t val_dtype, int64_t M, int64_t K, int64_t nnz,
+                       int32_t* out_colptr, int32_t* out_rowind, void* out_vals,
+                       int32_t* out_perm, void* workspace, size_t workspace_bytes,
+                       void* stream);
+
+/* Gather out_vals[p] = vals[perm[p]] for p < nnz (elements of val_dtype). */
+int spmm_gather_values(const void* vals, int32_t val_dtype, const int32_t* perm, int64_t nnz,
+                       void* out_vals, void* stream);
+
+/*
+ * spmm_sddmm_csr -- out_vals[e] = sum_n dC[row_e, n] * B[col_e, n] for every
+ *   nonzero e of A's pattern: the gradient of sum(dC .* (A B)) with respect to
+ *   A's values.  dC device float M x N (stride lddc); B device of b_dtype
+ *   (F32 or BF16) K x N (stride ldb); out_vals device float[nnz].
+ *   plan: a plan of the same A with tile_cols == 1 (or NULL: built inside the
+ *   workspace, sized by spmm_csr_workspace_size with tile grid 1 x 1).
+ */
+int spmm_sddmm_csr(const int32_t* A_rowptr, const int32_t* A_colind, const float* dC,
+                   int64_t lddc, const void* B, int32_t b_dtype, int64_t ldb, float* out_vals,
+                   int64_t M, int64_t K, int64_t N, int64_t nnz, spmm_plan plan,
+                   void* workspace, size_t workspace_bytes, void* stream);
+
+/*
+ * spmm_quantize_rows -- store a float32 matrix in a narrower type.
+ *   X device float rows x cols (stride ldx).  dtype F16 or BF16: Xq = round-
+ *   to-nearest-even of X, `scale` ignored (may be NULL).  dtype E4M3: per row,
+ *   s = amax|X[r,:]| / 448 computed in FP32 (s = 1 for an all-zero row),
+ *   Xq = E4M3(X / s) rounded to nearest even with saturation to +-448, and
+ *   scale[r] = s (device float[rows], required).  Xq stride ldq elements.
+ */
+int spmm_quantize_rows(const float* X, int64_t rows, int64_t cols, int64_t ldx, int32_t dtype,
+                       void* Xq, int64_t ldq, float* scale, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPMM_GB300_H */

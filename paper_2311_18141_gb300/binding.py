@@ -1,0 +1,258 @@
+"""Thin ctypes binding of the C ABI in include/spmm_gb300.h.
+
+Functions carry the C names and only marshal arguments: torch tensors become
+device pointers, the current torch stream becomes the cudaStream_t, and a
+non-zero status becomes an ``SpmmError``.  Every step of the computation runs
+in the CUDA library; if the library cannot be loaded, importing this module's
+functions raises, and there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libspmm_gb300.so")
+
+SPMM_OK = 0
+SPMM_ERR_INVALID_ARG = -1
+SPMM_ERR_MISALIGNED = -2
+SPMM_ERR_UNSUPPORTED = -3
+SPMM_ERR_CUDA = -4
+SPMM_ERR_BAD_CSR = -5
+SPMM_ERR_TIMEOUT = -6
+SPMM_ERR_WORKSPACE = -7
+SPMM_ERR_PLAN_MISMATCH = -8
+SPMM_ERR_INTERNAL = -9
+
+SPMM_F32, SPMM_F16, SPMM_BF16, SPMM_E4M3 = 0, 1, 2, 3
+
+EXPORTED = [
+    "spmm_status_string", "spmm_version", "spmm_plan_create", "spmm_plan_destroy",
+    "spmm_plan_workspace_size", "spmm_plan_units", "spmm_csr_workspace_size", "spmm_csr",
+    "spmm_csr_validate", "spmm_get_device_status", "spmm_csr_transpose_workspace_size",
+    "spmm_csr_transpose", "spmm_gather_values", "spmm_sddmm_csr", "spmm_quantize_rows",
+]
+
+
+class SpmmError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} ({status})")
+
+
+class spmm_tuning(ctypes.Structure):
+    _fields_ = [("chunk_items", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("tile_order", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(path: str | None = None):
+    """Load libspmm_gb300.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = path or LIB_PATH
+        if not os.path.exists(path):
+            raise ImportError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+        lib = ctypes.CDLL(path)
+        i32, i64, vp, f32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p, ctypes.c_float
+        sz = ctypes.c_size_t
+        lib.spmm_status_string.argtypes = [ctypes.c_int]
+        lib.spmm_status_string.restype = ctypes.c_char_p
+        lib.spmm_version.restype = ctypes.c_int
+        lib.spmm_plan_create.argtypes = [ctypes.POINTER(vp), vp, i64, i64, i64, i64, i32, i32,
+                                         ctypes.POINTER(spmm_tuning), vp]
+        lib.spmm_plan_destroy.argtypes = [vp]
+        lib.spmm_plan_workspace_size.argtypes = [vp, ctypes.POINTER(sz)]
+        lib.spmm_plan_units.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        lib.spmm_csr_workspace_size.argtypes = [i64, i64, i64, i32, i32,
+                                                ctypes.POINTER(spmm_tuning), ctypes.POINTER(sz)]
+        lib.spmm_csr.argtypes = [vp, vp, vp, i32, vp, vp, i32, vp, i64, vp, i64, i64, i64, i64,
+                                 i64, i32, i32, f32, vp, vp, sz, vp]
+        lib.spmm_csr_validate.argtypes = [vp, vp, i64, i64, i64, vp, sz, vp]
+        lib.spmm_get_device_status.argtypes = [vp, ctypes.POINTER(i32), vp]
+        lib.spmm_csr_transpose_workspace_size.argtypes = [i64, i64, i64, ctypes.POINTER(sz)]
+        lib.spmm_csr_transpose.argtypes = [vp, vp, vp, i32, i64, i64, i64, vp, vp, vp, vp, vp,
+                                           sz, vp]
+        lib.spmm_gather_values.argtypes = [vp, i32, vp, i64, vp, vp]
+        lib.spmm_sddmm_csr.argtypes = [vp, vp, vp, i64, vp, i32, i64, vp, i64, i64, i64, i64, vp,
+                                       vp, sz, vp]
+        lib.spmm_quantize_rows.argtypes = [vp, i64, i64, i64, i32, vp, i64, vp, vp]
+        for name in EXPORTED:
+            if name not in ("spmm_status_string",):
+                getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def status_string(status: int) -> str:
+    try:
+        return load_library().spmm_status_string(int(status)).decode()
+    except ImportError:
+        return "library not loaded"
+
+
+def _check(status: int, where: str) -> None:
+    if status != SPMM_OK:
+        raise SpmmError(status, where)
+
+
+def dtype_code(t: torch.dtype) -> int:
+    if t == torch.float32:
+        return SPMM_F32
+    if t == torch.float16:
+        return SPMM_F16
+    if t == torch.bfloat16:
+        return SPMM_BF16
+    if t in (torch.float8_e4m3fn, torch.uint8):
+        return SPMM_E4M3
+    raise TypeError(f"unsupported dtype {t}")
+
+
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def make_tuning(chunk_items=0, warps_per_cta=0, ctas_per_sm=0, tile_order=0) -> spmm_tuning:
+    t = spmm_tuning()
+    t.chunk_items, t.warps_per_cta = int(chunk_items), int(warps_per_cta)
+    t.ctas_per_sm, t.tile_order = int(ctas_per_sm), int(tile_order)
+    return t
+
+
+def workspace(nbytes: int, device=None) -> torch.Tensor:
+    """Device scratch of at least ``nbytes`` (256-byte aligned by the caching allocator)."""
+    return torch.zeros(max(int(nbytes), 256), dtype=torch.uint8, device=device or "cuda")
+
+
+class Plan:
+    """Owner of a spmm_plan handle (spmm_plan_create / spmm_plan_destroy)."""
+
+    def __init__(self, rowptr: torch.Tensor, M: int, K: int, nnz: int, N: int,
+                 tile_rows: int = 1, tile_cols: int = 1, tuning: spmm_tuning | None = None,
+                 stream=None):
+        lib = load_library()
+        self.handle = ctypes.c_void_p()
+        self.M, self.K, self.nnz, self.N = int(M), int(K), int(nnz), int(N)
+        self.tile_rows, self.tile_cols = int(tile_rows), int(tile_cols)
+        tp = ctypes.byref(tuning) if tuning is not None else None
+        _check(lib.spmm_plan_create(ctypes.byref(self.handle), _ptr(rowptr), self.M, self.K,
+                                    self.nnz, self.N, self.tile_rows, self.tile_cols, tp,
+                                    _stream(stream)), "spmm_plan_create")
+        n = ctypes.c_size_t()
+        _check(lib.spmm_plan_workspace_size(self.handle, ctypes.byref(n)),
+               "spmm_plan_workspace_size")
+        self.workspace_bytes = int(n.value)
+
+    def units(self) -> tuple[int, int]:
+        c, u = ctypes.c_int64(), ctypes.c_int64()
+        _check(load_library().spmm_plan_units(self.handle, ctypes.byref(c), ctypes.byref(u)),
+               "spmm_plan_units")
+        return int(c.value), int(u.value)
+
+    def close(self):
+        if self.handle:
+            load_library().spmm_plan_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def spmm_csr_workspace_size(M: int, nnz: int, N: int, tile_rows: int = 1,
+                            tile_cols: int = 1) -> int:
+    n = ctypes.c_size_t()
+    _check(load_library().spmm_csr_workspace_size(int(M), int(nnz), int(N), int(tile_rows),
+                                                  int(tile_cols), None, ctypes.byref(n)),
+           "spmm_csr_workspace_size")
+    return int(n.value)
+
+
+def spmm_csr(rowptr, colind, vals, B, C, M, K, N, nnz, *, a_scale=None, b_scale=None,
+             tile_rows=0, tile_cols=0, beta=0.0, plan: Plan | None = None, ws=None,
+             stream=None, ldb=None, ldc=None) -> None:
+    """C = beta*C + diag(a_scale) A (diag(b_scale) B) through the C ABI."""
+    lib = load_library()
+    if plan is None and tile_rows == 0:
+        tile_rows = 1
+    if plan is None and tile_cols == 0:
+        tile_cols = 1
+    ldb = B.stride(0) if ldb is None else ldb
+    ldc = C.stride(0) if ldc is None else ldc
+    ws_bytes = ws.numel() * ws.element_size() if ws is not None else 0
+    _check(lib.spmm_csr(_ptr(rowptr), _ptr(colind), _ptr(vals), dtype_code(vals.dtype),
+                        _ptr(a_scale), _ptr(B), dtype_code(B.dtype), _ptr(b_scale), int(ldb),
+                        _ptr(C), int(ldc), int(M), int(K), int(N), int(nnz), int(tile_rows),
+                        int(tile_cols), float(beta), plan.handle if plan is not None else None,
+                        _ptr(ws), int(ws_bytes), _stream(stream)), "spmm_csr")
+
+
+def spmm_csr_validate(rowptr, colind, M, K, nnz, ws, stream=None) -> None:
+    _check(load_library().spmm_csr_validate(_ptr(rowptr), _ptr(colind), int(M), int(K), int(nnz),
+                                            _ptr(ws), ws.numel() * ws.element_size(),
+                                            _stream(stream)), "spmm_csr_validate")
+
+
+def spmm_get_device_status(ws, stream=None) -> int:
+    st = ctypes.c_int32()
+    _check(load_library().spmm_get_device_status(_ptr(ws), ctypes.byref(st), _stream(stream)),
+           "spmm_get_device_status")
+    return int(st.value)
+
+
+def spmm_csr_transpose_workspace_size(M, K, nnz) -> int:
+    n = ctypes.c_size_t()
+    _check(load_library().spmm_csr_transpose_workspace_size(int(M), int(K), int(nnz),
+                                                            ctypes.byref(n)),
+           "spmm_csr_transpose_workspace_size")
+    return int(n.value)
+
+
+def spmm_csr_transpose(rowptr, colind, vals, M, K, nnz, out_colptr, out_rowind, out_vals=None,
+                       out_perm=None, ws=None, stream=None) -> None:
+    dt = dtype_code(vals.dtype) if vals is not None else SPMM_F32
+    _check(load_library().spmm_csr_transpose(
+        _ptr(rowptr), _ptr(colind), _ptr(vals), dt, int(M), int(K), int(nnz), _ptr(out_colptr),
+        _ptr(out_rowind), _ptr(out_vals), _ptr(out_perm), _ptr(ws),
+        ws.numel() * ws.element_size() if ws is not None else 0, _stream(stream)),
+        "spmm_csr_transpose")
+
+
+def spmm_gather_values(vals, perm, nnz, out_vals, stream=None) -> None:
+    _check(load_library().spmm_gather_values(_ptr(vals), dtype_code(vals.dtype), _ptr(perm),
+                                             int(nnz), _ptr(out_vals), _stream(stream)),
+           "spmm_gather_values")
+
+
+def spmm_sddmm_csr(rowptr, colind, dC, B, out_vals, M, K, N, nnz, plan: Plan | None = None,
+                   ws=None, stream=None) -> None:
+    _check(load_library().spmm_sddmm_csr(
+        _ptr(rowptr), _ptr(colind), _ptr(dC), int(dC.stride(0)), _ptr(B), dtype_code(B.dtype),
+        int(B.stride(0)), _ptr(out_vals), int(M), int(K), int(N), int(nnz),
+        plan.handle if plan is not None else None, _ptr(ws),
+        ws.numel() * ws.element_size() if ws is not None else 0, _stream(stream)),
+        "spmm_sddmm_csr")
+
+
+def spmm_quantize_rows(X, dtype: int, Xq, scale=None, stream=None) -> None:
+    rows, cols = X.shape
+    _check(load_library().spmm_quantize_rows(_ptr(X), rows, cols, int(X.stride(0)), int(dtype),
+                                             _ptr(Xq), int(Xq.stride(0)), _ptr(scale),
+                                             _stream(stream)), "spmm_quantize_rows")

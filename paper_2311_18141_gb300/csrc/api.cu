@@ -1,0 +1,303 @@
+// C ABI entry points: argument checks, plans, workspace layout and dispatch.
+#include <stdlib.h>
+#include <string.h>
+
+#include "api_internal.cuh"
+#include "launch.cuh"
+#include "plan.cuh"
+
+using namespace spmm;
+
+struct spmm_plan_s {
+    int device;
+    int64_t M, K, nnz, N;
+    int32_t TR, TC, RB, D;
+    int64_t cap;          // chunk capacity (upper bound of chunks)
+    spmm_tuning tuning;
+    void* mem;            // device plan arrays
+    int32_t* blk_base;
+    int32_t* bnd_row;
+    int32_t* bnd_nnz;
+};
+
+namespace spmm {
+
+int device_sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 148;
+    return n;
+}
+
+int elem_bytes(int dt) {
+    switch (dt) {
+        case SPMM_F32: return 4;
+        case SPMM_F16: case SPMM_BF16: return 2;
+        case SPMM_E4M3: return 1;
+        default: return 0;
+    }
+}
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Scratch layout of one call: [status 64 B][tile_ctr T][piece_cnt cap*TC] pad
+// 256 [slots 2*cap*N floats].
+struct Scratch {
+    size_t counters_off, counters_bytes, slots_off, total;
+};
+
+static Scratch scratch_layout(int32_t TR, int32_t TC, int64_t cap, int64_t N) {
+    Scratch s;
+    s.counters_off = kStatusBytes;
+    s.counters_bytes = 4 * ((size_t)TR * TC + (size_t)cap * TC);
+    s.slots_off = (s.counters_off + s.counters_bytes + 255) / 256 * 256;
+    s.total = s.slots_off + 4 * (size_t)2 * cap * N;
+    s.total = (s.total + 255) / 256 * 256;
+    return s;
+}
+
+void resolve_tuning(const spmm_tuning* in, spmm_tuning* out) {
+    memset(out, 0, sizeof(*out));
+    if (in) *out = *in;
+    if (out->warps_per_cta != 4 && out->warps_per_cta != 8) out->warps_per_cta = 8;
+    if (out->ctas_per_sm < 0) out->ctas_per_sm = 0;
+    if (out->tile_order != 1) out->tile_order = 0;
+    if (out->chunk_items < 0) out->chunk_items = 0;
+}
+
+// Column-block width for N split in TC blocks of B type `dt`: ceil(N/TC)
+// rounded up to whole 16-byte vectors.  0 if the grid leaves a block empty.
+int64_t column_block_width(int64_t N, int32_t TC, int dt) {
+    const int epv = 16 / elem_bytes(dt);
+    int64_t w = (N + TC - 1) / TC;
+    w = (w + epv - 1) / epv * epv;
+    if (w <= 0 || (int64_t)(TC - 1) * w >= N) return 0;
+    return w;
+}
+
+// Pick (lanes per nonzero, vectors per lane) covering `nvec` 16-byte vectors.
+bool pick_shape(int64_t nvec, int* lpn, int* vpl) {
+    if (nvec <= 0) return false;
+    if (nvec <= 32) {
+        int l = 2;
+        while (l < nvec) l <<= 1;
+        *lpn = l;
+        *vpl = 1;
+        return true;
+    }
+    *lpn = 32;
+    if (nvec <= 64) { *vpl = 2; return true; }
+    if (nvec <= 128) { *vpl = 4; return true; }
+    return false;
+}
+
+int plan_view(spmm_plan plan, int64_t M, int64_t K, int64_t nnz, int64_t N, int32_t* TR,
+              int32_t* TC, int32_t* RB, int32_t* D, int64_t* cap, int32_t** blk_base,
+              int32_t** bnd_row, int32_t** bnd_nnz) {
+    if (!plan) return SPMM_ERR_INVALID_ARG;
+    if (plan->M != M || plan->K != K || plan->nnz != nnz || plan->N != N)
+        return SPMM_ERR_PLAN_MISMATCH;
+    *TR = plan->TR; *TC = plan->TC; *RB = plan->RB; *D = plan->D; *cap = plan->cap;
+    *blk_base = plan->blk_base; *bnd_row = plan->bnd_row; *bnd_nnz = plan->bnd_nnz;
+    return SPMM_OK;
+}
+
+}  // namespace spmm
+
+extern "C" {
+
+const char* spmm_status_string(int status) {
+    switch (status) {
+        case SPMM_OK: return "ok";
+        case SPMM_ERR_INVALID_ARG: return "invalid argument";
+        case SPMM_ERR_MISALIGNED: return "misaligned pointer, stride or width";
+        case SPMM_ERR_UNSUPPORTED: return "unsupported dtype or width";
+        case SPMM_ERR_CUDA: return "CUDA runtime error";
+        case SPMM_ERR_BAD_CSR: return "malformed CSR";
+        case SPMM_ERR_TIMEOUT: return "device wait timed out";
+        case SPMM_ERR_WORKSPACE: return "workspace missing or too small";
+        case SPMM_ERR_PLAN_MISMATCH: return "plan does not match the call";
+        case SPMM_ERR_INTERNAL: return "internal plan check failed";
+        default: return "unknown status";
+    }
+}
+
+int spmm_version(void) { return 100; }
+
+static int check_shape(int64_t M, int64_t K, int64_t nnz, int64_t N, int32_t TR, int32_t TC) {
+    const int64_t lim = (int64_t)1 << 30;
+    if (M < 0 || K < 0 || nnz < 0 || N < 0) return SPMM_ERR_INVALID_ARG;
+    if (M >= lim * 2 - (1 << 20) || K >= lim * 2 - (1 << 20) || nnz >= lim * 2 - 1)
+        return SPMM_ERR_INVALID_ARG;
+    if (N > (1 << 20)) return SPMM_ERR_INVALID_ARG;
+    if (TR < 1 || TR > 65536 || TC < 1 || TC > 4096) return SPMM_ERR_INVALID_ARG;
+    if (M > 0 && nnz > 0 && K == 0) return SPMM_ERR_INVALID_ARG;
+    return SPMM_OK;
+}
+
+int spmm_plan_create(spmm_plan* plan, const int32_t* A_rowptr, int64_t M, int64_t K,
+                     int64_t nnz, int64_t N, int32_t tile_rows, int32_t tile_cols,
+                     const spmm_tuning* tuning, void* stream) {
+    if (!plan) return SPMM_ERR_INVALID_ARG;
+    *plan = nullptr;
+    int st = check_shape(M, K, nnz, N, tile_rows, tile_cols);
+    if (st) return st;
+    if (!A_rowptr) return SPMM_ERR_INVALID_ARG;
+    spmm_plan_s* p = (spmm_plan_s*)calloc(1, sizeof(spmm_plan_s));
+    if (!p) return SPMM_ERR_INVALID_ARG;
+    if (cudaGetDevice(&p->device) != cudaSuccess) { free(p); return SPMM_ERR_CUDA; }
+    p->M = M; p->K = K; p->nnz = nnz; p->N = N;
+    p->TR = tile_rows; p->TC = tile_cols;
+    p->RB = (int32_t)((M + tile_rows - 1) / tile_rows);
+    if (p->RB < 1) p->RB = 1;
+    resolve_tuning(tuning, &p->tuning);
+    p->D = p->tuning.chunk_items > 0 ? p->tuning.chunk_items
+                                    : plan_default_chunk(M, nnz, tile_cols, device_sm_count());
+    p->tuning.chunk_items = p->D;
+    p->cap = plan_chunk_cap(M, nnz, tile_rows, p->D);
+    const size_t bytes = plan_array_bytes(tile_rows, p->cap);
+    if (cudaMalloc(&p->mem, bytes) != cudaSuccess) { free(p); return SPMM_ERR_CUDA; }
+    plan_carve(p->mem, tile_rows, p->cap, &p->blk_base, &p->bnd_row, &p->bnd_nnz);
+    cudaError_t e = plan_build(A_rowptr, M, p->TR, p->RB, p->D, p->cap, p->blk_base, p->bnd_row,
+                               p->bnd_nnz, (cudaStream_t)stream);
+    if (e != cudaSuccess) { cudaFree(p->mem); free(p); return SPMM_ERR_CUDA; }
+    *plan = p;
+    return SPMM_OK;
+}
+
+int spmm_plan_destroy(spmm_plan plan) {
+    if (!plan) return SPMM_OK;
+    cudaDeviceSynchronize();
+    cudaFree(plan->mem);
+    free(plan);
+    return SPMM_OK;
+}
+
+int spmm_plan_workspace_size(spmm_plan plan, size_t* bytes) {
+    if (!plan || !bytes) return SPMM_ERR_INVALID_ARG;
+    *bytes = scratch_layout(plan->TR, plan->TC, plan->cap, plan->N).total;
+    return SPMM_OK;
+}
+
+int spmm_plan_units(spmm_plan plan, int64_t* chunks, int64_t* units) {
+    if (!plan) return SPMM_ERR_INVALID_ARG;
+    int32_t n = 0;
+    if (cudaMemcpy(&n, plan->blk_base + plan->TR, sizeof(n), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return SPMM_ERR_CUDA;
+    if (chunks) *chunks = n;
+    if (units) *units = (int64_t)n * plan->TC;
+    return SPMM_OK;
+}
+
+int spmm_csr_workspace_size(int64_t M, int64_t nnz, int64_t N, int32_t tile_rows,
+                            int32_t tile_cols, const spmm_tuning* tuning, size_t* bytes) {
+    if (!bytes) return SPMM_ERR_INVALID_ARG;
+    int st = check_shape(M, 1, nnz, N, tile_rows, tile_cols);
+    if (st) return st;
+    (void)tuning;  // a call without a plan always uses the default tuning
+    const int32_t D = plan_default_chunk(M, nnz, tile_cols, device_sm_count());
+    const int64_t cap = plan_chunk_cap(M, nnz, tile_rows, D);
+    *bytes = plan_array_bytes(tile_rows, cap) + scratch_layout(tile_rows, tile_cols, cap, N).total;
+    return SPMM_OK;
+}
+
+int spmm_csr(const int32_t* A_rowptr, const int32_t* A_colind, const void* A_vals,
+             int32_t a_dtype, const float* A_row_scale, const void* B, int32_t b_dtype,
+             const float* B_row_scale, int64_t ldb, float* C, int64_t ldc, int64_t M,
+             int64_t K, int64_t N, int64_t nnz, int32_t tile_rows, int32_t tile_cols,
+             float beta, spmm_plan plan, void* workspace, size_t workspace_bytes,
+             void* stream) {
+    if (plan) {
+        if (tile_rows == 0) tile_rows = plan->TR;
+        if (tile_cols == 0) tile_cols = plan->TC;
+    }
+    int st = check_shape(M, K, nnz, N, tile_rows, tile_cols);
+    if (st) return st;
+    if (elem_bytes(a_dtype) == 0 || elem_bytes(b_dtype) == 0) return SPMM_ERR_UNSUPPORTED;
+    if (M == 0 || N == 0) return SPMM_OK;
+    if (!A_rowptr || !C || (nnz > 0 && (!A_colind || !A_vals || !B))) return SPMM_ERR_INVALID_ARG;
+    if (ldb < N || ldc < N) return SPMM_ERR_INVALID_ARG;
+    const int eb = elem_bytes(b_dtype);
+    const int epv = 16 / eb;
+    if (N % epv != 0 || (ldb * eb) % 16 != 0 || (ldc * 4) % 16 != 0 || !aligned16(C) ||
+        (B && !aligned16(B)))
+        return SPMM_ERR_MISALIGNED;
+    const int64_t W = column_block_width(N, tile_cols, b_dtype);
+    if (W == 0) return SPMM_ERR_INVALID_ARG;
+    int lpn = 0, vpl = 0;
+    if (!pick_shape(W / epv, &lpn, &vpl)) return SPMM_ERR_UNSUPPORTED;
+    if (!workspace || ((uintptr_t)workspace & 255u)) return SPMM_ERR_WORKSPACE;
+
+    cudaStream_t s = (cudaStream_t)stream;
+    char* ws = static_cast<char*>(workspace);
+    int32_t TR = tile_rows, TC = tile_cols, RB, D;
+    int64_t cap;
+    int32_t *blk_base, *bnd_row, *bnd_nnz;
+    spmm_tuning tun;
+    if (plan) {
+        if (plan->M != M || plan->nnz != nnz || plan->N != N || plan->TR != TR ||
+            plan->TC != TC || plan->K != K)
+            return SPMM_ERR_PLAN_MISMATCH;
+        RB = plan->RB; D = plan->D; cap = plan->cap;
+        blk_base = plan->blk_base; bnd_row = plan->bnd_row; bnd_nnz = plan->bnd_nnz;
+        tun = plan->tuning;
+    } else {
+        resolve_tuning(nullptr, &tun);
+        RB = (int32_t)((M + TR - 1) / TR);
+        D = plan_default_chunk(M, nnz, TC, device_sm_count());
+        cap = plan_chunk_cap(M, nnz, TR, D);
+        const size_t pb = plan_array_bytes(TR, cap);
+        const Scratch sc = scratch_layout(TR, TC, cap, N);
+        if (workspace_bytes < pb + sc.total) return SPMM_ERR_WORKSPACE;
+        plan_carve(ws, TR, cap, &blk_base, &bnd_row, &bnd_nnz);
+        if (plan_build(A_rowptr, M, TR, RB, D, cap, blk_base, bnd_row, bnd_nnz, s) != cudaSuccess)
+            return SPMM_ERR_CUDA;
+        ws += pb;
+        workspace_bytes -= pb;
+    }
+    const Scratch sc = scratch_layout(TR, TC, cap, N);
+    if (workspace_bytes < sc.total) return SPMM_ERR_WORKSPACE;
+
+    Problem p;
+    p.rowptr = A_rowptr; p.colind = A_colind; p.vals = A_vals; p.a_scale = A_row_scale;
+    p.B = B; p.b_scale = B_row_scale; p.C = C; p.ldb = ldb; p.ldc = ldc;
+    p.M = (int32_t)M; p.N = (int32_t)N; p.a_dtype = a_dtype; p.beta = beta;
+    p.TR = TR; p.TC = TC; p.RB = RB; p.W = (int32_t)W; p.D = D;
+    p.blk_base = blk_base; p.bnd_row = bnd_row; p.bnd_nnz = bnd_nnz;
+    p.status = reinterpret_cast<int32_t*>(ws);
+    p.tile_ctr = reinterpret_cast<int32_t*>(ws + sc.counters_off);
+    p.piece_cnt = p.tile_ctr + (size_t)TR * TC;
+    p.slots = reinterpret_cast<float*>(ws + sc.slots_off);
+    if (cudaMemsetAsync(ws + sc.counters_off, 0, sc.counters_bytes, s) != cudaSuccess)
+        return SPMM_ERR_CUDA;
+    LaunchOpts o;
+    o.warps_per_cta = tun.warps_per_cta;
+    o.ctas_per_sm = tun.ctas_per_sm;
+    o.tile_order = tun.tile_order;
+    o.units = cap * TC;
+    cudaError_t e;
+    switch (b_dtype) {
+        case SPMM_F32: e = launch_spmm_f32(lpn, vpl, p, o, s); break;
+        case SPMM_F16: e = launch_spmm_f16(lpn, vpl, p, o, s); break;
+        case SPMM_BF16: e = launch_spmm_bf16(lpn, vpl, p, o, s); break;
+        default: e = launch_spmm_e4m3(lpn, vpl, p, o, s); break;
+    }
+    return e == cudaSuccess ? SPMM_OK : SPMM_ERR_CUDA;
+}
+
+int spmm_get_device_status(void* workspace, int32_t* status, void* stream) {
+    if (!workspace || !status) return SPMM_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t h[2] = {0, 0};
+    if (cudaMemcpyAsync(h, workspace, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return SPMM_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SPMM_ERR_CUDA;
+    if (cudaMemsetAsync(workspace, 0, sizeof(h), s) != cudaSuccess) return SPMM_ERR_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return SPMM_ERR_CUDA;
+    if (h[0] != 0) *status = h[0];
+    else if (h[1] != 0) *status = SPMM_ERR_INTERNAL;
+    else *status = SPMM_OK;
+    return SPMM_OK;
+}
+
+}  // extern "C"

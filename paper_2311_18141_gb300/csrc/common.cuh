@@ -1,0 +1,201 @@
+// Device helpers shared by the sm_103a kernels: cache-hinted loads and
+// stores, element decode, packed FP32 FMA, and the argument blocks.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include "../../include/spmm_gb300.h"
+
+namespace spmm {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---------------------------------------------------------------- loads ----
+
+// Streaming 32-bit load that skips L1 (CSR arrays are touched once per unit;
+// they stay in L2 for the other column blocks of the same chunk).
+__device__ __forceinline__ int32_t ld_stream_i32(const int32_t* p) {
+    int32_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_stream_u16(const void* p) {
+    uint16_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.u16 %0, [%1];" : "=h"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_stream_u8(const void* p) {
+    uint16_t v;
+    asm volatile("ld.global.nc.L1::no_allocate.u8 %0, [%1];" : "=h"(v) : "l"(p));
+    return v;
+}
+
+// 16-byte read-only load of a B row vector (L1-cacheable: hot rows repeat).
+__device__ __forceinline__ uint4 ld_b16(const void* p) {
+    return __ldg(reinterpret_cast<const uint4*>(p));
+}
+
+// Relaxed GPU-scope read of a work counter.
+__device__ __forceinline__ int32_t ld_relaxed(const int32_t* p) {
+    int32_t v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+// 16-byte L2 (coherent) load, used to read partial rows written by other SMs.
+__device__ __forceinline__ float4 ld_cg_f4(const float* p) {
+    return __ldcg(reinterpret_cast<const float4*>(p));
+}
+
+// Streaming 16-byte store (C is written once).
+__device__ __forceinline__ void st_cs_f4(float* p, float4 v) {
+    __stcs(reinterpret_cast<float4*>(p), v);
+}
+__device__ __forceinline__ void st_cg_f4(float* p, float4 v) {
+    __stcg(reinterpret_cast<float4*>(p), v);
+}
+
+// ---------------------------------------------------------------- math ----
+
+// acc[0..1] += a * b[0..1] as one packed FP32 FMA (fma.rn.f32x2, sm_100+).
+__device__ __forceinline__ void ffma2(float& c0, float& c1, float a, float b0, float b1) {
+#if defined(SPMM_USE_FFMA2) && defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000)
+    asm("{\n\t.reg .b64 ra, rb, rc;\n\t"
+        "mov.b64 ra, {%2, %2};\n\t"
+        "mov.b64 rb, {%3, %4};\n\t"
+        "mov.b64 rc, {%0, %1};\n\t"
+        "fma.rn.f32x2 rc, ra, rb, rc;\n\t"
+        "mov.b64 {%0, %1}, rc;\n\t}"
+        : "+f"(c0), "+f"(c1)
+        : "f"(a), "f"(b0), "f"(b1));
+#else
+    c0 = fmaf(a, b0, c0);
+    c1 = fmaf(a, b1, c1);
+#endif
+}
+
+// -------------------------------------------------------------- decode ----
+
+// Element traits of B's storage type: EPV = elements per 16-byte vector.
+struct TagF32 { static constexpr int EPV = 4;  static constexpr int dtype = SPMM_F32; };
+struct TagF16 { static constexpr int EPV = 8;  static constexpr int dtype = SPMM_F16; };
+struct TagBF16 { static constexpr int EPV = 8; static constexpr int dtype = SPMM_BF16; };
+struct TagE4M3 { static constexpr int EPV = 16; static constexpr int dtype = SPMM_E4M3; };
+
+__device__ __forceinline__ float bf16lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf16hi(uint32_t w) { return __uint_as_float(w & 0xffff0000u); }
+
+__device__ __forceinline__ float2 h2f2(uint32_t w) {
+    __half2 h = *reinterpret_cast<const __half2*>(&w);
+    return __half22float2(h);
+}
+
+// two E4M3 codes (low 16 bits of w) -> two floats, exactly (E4M3 is a subset of f16)
+__device__ __forceinline__ float2 e4m3x2_to_f2(uint16_t w) {
+    uint32_t h2;
+    asm("cvt.rn.f16x2.e4m3x2 %0, %1;" : "=r"(h2) : "h"(w));
+    return h2f2(h2);
+}
+
+// acc[0..EPV) += a * decode(v)
+template <typename Tag>
+__device__ __forceinline__ void fma_vec(float* acc, float a, const uint4& v);
+
+template <>
+__device__ __forceinline__ void fma_vec<TagF32>(float* acc, float a, const uint4& v) {
+    ffma2(acc[0], acc[1], a, __uint_as_float(v.x), __uint_as_float(v.y));
+    ffma2(acc[2], acc[3], a, __uint_as_float(v.z), __uint_as_float(v.w));
+}
+template <>
+__device__ __forceinline__ void fma_vec<TagBF16>(float* acc, float a, const uint4& v) {
+    ffma2(acc[0], acc[1], a, bf16lo(v.x), bf16hi(v.x));
+    ffma2(acc[2], acc[3], a, bf16lo(v.y), bf16hi(v.y));
+    ffma2(acc[4], acc[5], a, bf16lo(v.z), bf16hi(v.z));
+    ffma2(acc[6], acc[7], a, bf16lo(v.w), bf16hi(v.w));
+}
+template <>
+__device__ __forceinline__ void fma_vec<TagF16>(float* acc, float a, const uint4& v) {
+    float2 f;
+    f = h2f2(v.x); ffma2(acc[0], acc[1], a, f.x, f.y);
+    f = h2f2(v.y); ffma2(acc[2], acc[3], a, f.x, f.y);
+    f = h2f2(v.z); ffma2(acc[4], acc[5], a, f.x, f.y);
+    f = h2f2(v.w); ffma2(acc[6], acc[7], a, f.x, f.y);
+}
+template <>
+__device__ __forceinline__ void fma_vec<TagE4M3>(float* acc, float a, const uint4& v) {
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        float2 f0 = e4m3x2_to_f2((uint16_t)(w[q] & 0xffffu));
+        float2 f1 = e4m3x2_to_f2((uint16_t)(w[q] >> 16));
+        ffma2(acc[4 * q + 0], acc[4 * q + 1], a, f0.x, f0.y);
+        ffma2(acc[4 * q + 2], acc[4 * q + 3], a, f1.x, f1.y);
+    }
+}
+
+// Decode A's value e of runtime type `dt` (uniform across the warp).
+__device__ __forceinline__ float load_aval(const void* vals, int dt, int64_t e) {
+    switch (dt) {
+        case SPMM_F32:
+            return __int_as_float(ld_stream_i32(reinterpret_cast<const int32_t*>(vals) + e));
+        case SPMM_F16: {
+            uint32_t h = ld_stream_u16(reinterpret_cast<const uint16_t*>(vals) + e);
+            return __half2float(__ushort_as_half((unsigned short)h));
+        }
+        case SPMM_BF16: {
+            uint32_t h = ld_stream_u16(reinterpret_cast<const uint16_t*>(vals) + e);
+            return __uint_as_float(h << 16);
+        }
+        default: {
+            uint32_t q = ld_stream_u8(reinterpret_cast<const uint8_t*>(vals) + e);
+            return e4m3x2_to_f2((uint16_t)q).x;
+        }
+    }
+}
+
+// Position of the q-th (0-based) set bit of m; requires q < popc(m).  Binary
+// search on prefix popcounts; the result is always in [0, 31].
+__device__ __forceinline__ int nth_set_bit(unsigned m, int q) {
+    int pos = 0;
+    const int need = q + 1;
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1)
+        if (__popc(m & ((1u << (pos + w)) - 1u)) < need) pos += w;
+    return pos;
+}
+
+// ----------------------------------------------------------- arguments ----
+
+// One SpMM problem as the persistent kernel sees it.
+struct Problem {
+    const int32_t* rowptr;
+    const int32_t* colind;
+    const void* vals;
+    const float* a_scale;   // nullable, [M]
+    const void* B;
+    const float* b_scale;   // nullable, [K]
+    float* C;
+    int64_t ldb;            // elements
+    int64_t ldc;            // elements
+    int32_t M, N;
+    int32_t a_dtype;
+    float beta;
+    // plan
+    int32_t TR, TC, RB, W, D;
+    const int32_t* blk_base;  // [TR+1] chunk prefix per row block
+    const int32_t* bnd_row;   // boundary (row, nnz) at index blk_base[i] + i + c
+    const int32_t* bnd_nnz;
+    // per-call scratch
+    int32_t* tile_ctr;        // [TR*TC]
+    int32_t* piece_cnt;       // [chunks*TC]
+    float* slots;             // [2*chunks][N]
+    int32_t* status;          // status words
+};
+
+// Workspace layout (offsets in bytes from the workspace base).
+constexpr size_t kStatusBytes = 64;      // status[0]: validator, status[1]: internal
+
+}  // namespace spmm

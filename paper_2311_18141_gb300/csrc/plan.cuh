@@ -1,0 +1,23 @@
+// Host-side helpers for plan construction (merge-path chunk boundaries).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace spmm {
+
+// Upper bound on the number of chunks of all row blocks.
+int64_t plan_chunk_cap(int64_t M, int64_t nnz, int32_t TR, int32_t D);
+// Default merge-path items per chunk: about 16 units per resident warp.
+int32_t plan_default_chunk(int64_t M, int64_t nnz, int32_t TC, int sms);
+// Bytes of the plan arrays (blk_base, bnd_row, bnd_nnz), 256-byte padded.
+size_t plan_array_bytes(int32_t TR, int64_t cap);
+// Split a plan-array region into its three arrays.
+void plan_carve(void* base, int32_t TR, int64_t cap, int32_t** blk_base, int32_t** bnd_row,
+                int32_t** bnd_nnz);
+// Enqueue the two plan kernels on `s`.
+cudaError_t plan_build(const int32_t* rowptr, int64_t M, int32_t TR, int32_t RB, int32_t D,
+                       int64_t cap, int32_t* blk_base, int32_t* bnd_row, int32_t* bnd_nnz,
+                       cudaStream_t s);
+
+}  // namespace spmm

@@ -1,0 +1,11 @@
+// Persistent SpMM kernels with B stored as BF16.
+#include "spmm_launch_impl.cuh"
+
+namespace spmm {
+
+cudaError_t launch_spmm_bf16(int lpn, int vpl, const Problem& p, const LaunchOpts& o,
+                           cudaStream_t s) {
+    return launch_tag<TagBF16>(lpn, vpl, p, o, s);
+}
+
+}  // namespace spmm

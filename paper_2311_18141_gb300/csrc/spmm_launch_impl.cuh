@@ -1,0 +1,40 @@
+// Instantiates the persistent SpMM kernel for one B storage type.
+#pragma once
+
+#include "launch.cuh"
+#include "spmm_kernel.cuh"
+
+namespace spmm {
+
+template <class Tag, int LPN, int VPL>
+cudaError_t launch_one(const Problem& p, const LaunchOpts& o, cudaStream_t s) {
+    auto kern = spmm_csr_persistent<Tag, LPN, VPL>;
+    const int threads = o.warps_per_cta * 32;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    if (o.ctas_per_sm > 0 && o.ctas_per_sm < per_sm) per_sm = o.ctas_per_sm;
+    int64_t grid = (int64_t)device_sm_count() * per_sm;
+    const int64_t need = (o.units + o.warps_per_cta - 1) / o.warps_per_cta;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, threads, 0, s>>>(p, o.tile_order);
+    return cudaGetLastError();
+}
+
+template <class Tag>
+cudaError_t launch_tag(int lpn, int vpl, const Problem& p, const LaunchOpts& o, cudaStream_t s) {
+    switch (lpn * 10 + vpl) {
+        case 21: return launch_one<Tag, 2, 1>(p, o, s);
+        case 41: return launch_one<Tag, 4, 1>(p, o, s);
+        case 81: return launch_one<Tag, 8, 1>(p, o, s);
+        case 161: return launch_one<Tag, 16, 1>(p, o, s);
+        case 321: return launch_one<Tag, 32, 1>(p, o, s);
+        case 322: return launch_one<Tag, 32, 2>(p, o, s);
+        case 324: return launch_one<Tag, 32, 4>(p, o, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace spmm

@@ -1,0 +1,281 @@
+// CSR -> CSC (the CSR of A^T) on the device, for the backward dB = A^T dC.
+//
+// The nonzeros are sorted by column with a stable least-significant-digit
+// radix sort (8-bit digits) carrying each nonzero's CSR position e.  The CSR
+// order lists rows in increasing order, so stability leaves every column's
+// rows increasing and the output is the same on every run.  Then
+//   perm[p]      = e of the nonzero that lands at CSC position p,
+//   rowind[p]    = row of nonzero perm[p],
+//   vals_t[p]    = vals[perm[p]],
+//   colptr[c]    = first p whose column >= c (binary search of the sorted keys).
+// Each radix pass is three kernels: per-tile digit counts, one exclusive scan
+// over the digit-major count table, and a stable scatter in which every tile
+// ranks its keys in index order (warp match + per-warp digit counts).
+#include "api_internal.cuh"
+
+namespace spmm {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;                         // keys per thread per tile
+constexpr int kTile = kSortThreads * kSortItems;       // 4096 keys per tile
+constexpr int kRadix = 256;
+constexpr int kScanBlock = 1024;                       // scan: elements per block-thread group
+
+int device_sm_count();
+
+// row_of[e] = row containing nonzero e (one warp per row).
+__global__ void expand_rows_kernel(const int32_t* __restrict__ rowptr, int64_t M,
+                                   int32_t* __restrict__ row_of) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < M; r += nw) {
+        const int32_t a = rowptr[r], b = rowptr[r + 1];
+        for (int32_t e = a + lane; e < b; e += 32) row_of[e] = (int32_t)r;
+    }
+}
+
+// counts[d * ntiles + tile] = number of keys of the tile with digit d.
+__global__ void __launch_bounds__(kSortThreads)
+radix_count_kernel(const int32_t* __restrict__ keys, int64_t n, int shift, int64_t ntiles,
+                   int32_t* __restrict__ counts) {
+    __shared__ int32_t h[kRadix];
+    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) h[d] = 0;
+    __syncthreads();
+    const int64_t tile = blockIdx.x;
+    const int64_t base = tile * kTile;
+    for (int k = 0; k < kSortItems; ++k) {
+        const int64_t idx = base + (int64_t)k * kSortThreads + threadIdx.x;
+        if (idx < n) atomicAdd(&h[((uint32_t)keys[idx] >> shift) & 0xff], 1);
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) counts[(int64_t)d * ntiles + tile] = h[d];
+}
+
+// Exclusive scan, three phases: block sums, scan of block sums, block scan.
+__global__ void __launch_bounds__(1024)
+scan_block_sums_kernel(const int32_t* __restrict__ in, int64_t n, int64_t per_block,
+                       int64_t* __restrict__ sums) {
+    __shared__ int64_t red[1024];
+    const int64_t lo = (int64_t)blockIdx.x * per_block;
+    const int64_t hi = min(n, lo + per_block);
+    int64_t s = 0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) s += in[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 512; off > 0; off >>= 1) {
+        if ((int)threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) sums[blockIdx.x] = red[0];
+}
+
+__global__ void scan_sums_serial_kernel(int64_t* sums, int64_t nb) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int64_t run = 0;
+    for (int64_t b = 0; b < nb; ++b) {
+        const int64_t v = sums[b];
+        sums[b] = run;
+        run += v;
+    }
+}
+
+__global__ void __launch_bounds__(1024)
+scan_apply_kernel(int32_t* __restrict__ data, int64_t n, int64_t per_block,
+                  const int64_t* __restrict__ sums) {
+    __shared__ int64_t part[1024];
+    const int64_t lo = (int64_t)blockIdx.x * per_block;
+    const int64_t hi = min(n, lo + per_block);
+    const int64_t chunk = (per_block + blockDim.x - 1) / blockDim.x;
+    const int64_t a = min(hi, lo + (int64_t)threadIdx.x * chunk);
+    const int64_t b = min(hi, a + chunk);
+    int64_t s = 0;
+    for (int64_t i = a; i < b; ++i) s += data[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    // Hillis-Steele inclusive scan of the 1024 thread sums
+    for (int off = 1; off < 1024; off <<= 1) {
+        const int64_t v = (int)threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int64_t run = sums[blockIdx.x] + (threadIdx.x ? part[threadIdx.x - 1] : 0);
+    for (int64_t i = a; i < b; ++i) {
+        const int32_t v = data[i];
+        data[i] = (int32_t)run;
+        run += v;
+    }
+}
+
+// Stable scatter of one radix pass.  Keys of the tile are taken in rounds of
+// kSortThreads consecutive keys; within a round, warp w's keys precede warp
+// w+1's, and lanes are in index order, so ranks follow index order.
+__global__ void __launch_bounds__(kSortThreads)
+radix_scatter_kernel(const int32_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in,
+                     int64_t n, int shift, int64_t ntiles, const int32_t* __restrict__ offsets,
+                     int32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out) {
+    constexpr int W = kSortThreads / 32;
+    __shared__ int32_t base[kRadix];        // running position of each digit in this tile
+    __shared__ int32_t wcnt[W][kRadix];     // per-warp digit counts of the current round
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t tile = blockIdx.x;
+    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) base[d] = offsets[(int64_t)d * ntiles + tile];
+    for (int k = 0; k < kSortItems; ++k) {
+        for (int q = threadIdx.x; q < W * kRadix; q += kSortThreads) (&wcnt[0][0])[q] = 0;
+        __syncthreads();
+        const int64_t idx = tile * kTile + (int64_t)k * kSortThreads + threadIdx.x;
+        const bool ok = idx < n;
+        const int32_t key = ok ? keys_in[idx] : 0;
+        const int32_t val = ok ? (vals_in ? vals_in[idx] : (int32_t)idx) : 0;
+        const int d = ok ? (int)(((uint32_t)key >> shift) & 0xff) : kRadix;  // kRadix = none
+        const unsigned peers = __match_any_sync(kFull, d);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        if (ok && rank == 0) wcnt[warp][d] = __popc(peers);
+        __syncthreads();
+        // exclusive prefix over warps for each digit; advance the running base
+        for (int dd = threadIdx.x; dd < kRadix; dd += kSortThreads) {
+            int32_t run = base[dd];
+            for (int w = 0; w < W; ++w) {
+                const int32_t c = wcnt[w][dd];
+                wcnt[w][dd] = run;
+                run += c;
+            }
+            base[dd] = run;
+        }
+        __syncthreads();
+        if (ok) {
+            const int32_t pos = wcnt[warp][d] + rank;
+            keys_out[pos] = key;
+            vals_out[pos] = val;
+        }
+        __syncthreads();
+    }
+}
+
+// colptr[c] = lower_bound(sorted_keys, c), c in [0, K].
+__global__ void colptr_kernel(const int32_t* __restrict__ sorted, int64_t n, int64_t K,
+                              int32_t* __restrict__ colptr) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c <= K; c += stride) {
+        int64_t lo = 0, hi = n;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((int64_t)sorted[mid] < c) lo = mid + 1;
+            else hi = mid;
+        }
+        colptr[c] = (int32_t)lo;
+    }
+}
+
+template <typename T>
+__global__ void finish_kernel(const int32_t* __restrict__ perm, const int32_t* __restrict__ row_of,
+                              const T* __restrict__ vals, int64_t n, int32_t* __restrict__ rowind,
+                              T* __restrict__ vals_t, int32_t* __restrict__ perm_out) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += stride) {
+        const int32_t e = perm[p];
+        rowind[p] = row_of[e];
+        if (vals_t) vals_t[p] = vals[e];
+        if (perm_out) perm_out[p] = e;
+    }
+}
+
+struct TransposeLayout {
+    size_t row_of, keys0, keys1, vals0, vals1, counts, sums, total;
+    int64_t ntiles, ncounts, scan_blocks, per_block;
+};
+
+static size_t up256(size_t x) { return (x + 255) / 256 * 256; }
+
+static TransposeLayout transpose_layout(int64_t nnz) {
+    TransposeLayout L;
+    L.ntiles = (nnz + kTile - 1) / kTile;
+    if (L.ntiles < 1) L.ntiles = 1;
+    L.ncounts = L.ntiles * kRadix;
+    L.per_block = 64 * kScanBlock;
+    L.scan_blocks = (L.ncounts + L.per_block - 1) / L.per_block;
+    size_t off = 0;
+    const size_t a = up256(4 * (size_t)(nnz > 0 ? nnz : 1));
+    L.row_of = off; off += a;
+    L.keys0 = off; off += a;
+    L.keys1 = off; off += a;
+    L.vals0 = off; off += a;
+    L.vals1 = off; off += a;
+    L.counts = off; off += up256(4 * (size_t)L.ncounts);
+    L.sums = off; off += up256(8 * (size_t)L.scan_blocks);
+    L.total = off;
+    return L;
+}
+
+static unsigned grid_cap(int64_t work, int threads) {
+    int64_t g = (work + threads - 1) / threads;
+    const int64_t cap = (int64_t)device_sm_count() * 8;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (unsigned)g;
+}
+
+}  // namespace spmm
+
+using namespace spmm;
+
+extern "C" int spmm_csr_transpose_workspace_size(int64_t M, int64_t K, int64_t nnz,
+                                                 size_t* bytes) {
+    if (!bytes || M < 0 || K < 0 || nnz < 0) return SPMM_ERR_INVALID_ARG;
+    *bytes = transpose_layout(nnz).total;
+    return SPMM_OK;
+}
+
+extern "C" int spmm_csr_transpose(const int32_t* A_rowptr, const int32_t* A_colind,
+                                  const void* A_vals, int32_t val_dtype, int64_t M, int64_t K,
+                                  int64_t nnz, int32_t* out_colptr, int32_t* out_rowind,
+                                  void* out_vals, int32_t* out_perm, void* workspace,
+                                  size_t workspace_bytes, void* stream) {
+    if (M < 0 || K < 0 || nnz < 0 || nnz >= ((int64_t)1 << 31) - 1) return SPMM_ERR_INVALID_ARG;
+    if (K >= ((int64_t)1 << 31) - 1) return SPMM_ERR_INVALID_ARG;
+    if (!A_rowptr || !out_colptr || (nnz > 0 && (!A_colind || !out_rowind)))
+        return SPMM_ERR_INVALID_ARG;
+    if (out_vals && (!A_vals || elem_bytes(val_dtype) == 0)) return SPMM_ERR_INVALID_ARG;
+    const TransposeLayout L = transpose_layout(nnz);
+    if (!workspace || workspace_bytes < L.total || ((uintptr_t)workspace & 255u))
+        return SPMM_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    char* ws = static_cast<char*>(workspace);
+    if (nnz == 0) {
+        if (cudaMemsetAsync(out_colptr, 0, 4 * (size_t)(K + 1), s) != cudaSuccess) return SPMM_ERR_CUDA;
+        return SPMM_OK;
+    }
+    int32_t* row_of = reinterpret_cast<int32_t*>(ws + L.row_of);
+    int32_t* kb[2] = {reinterpret_cast<int32_t*>(ws + L.keys0), reinterpret_cast<int32_t*>(ws + L.keys1)};
+    int32_t* vb[2] = {reinterpret_cast<int32_t*>(ws + L.vals0), reinterpret_cast<int32_t*>(ws + L.vals1)};
+    int32_t* counts = reinterpret_cast<int32_t*>(ws + L.counts);
+    int64_t* sums = reinterpret_cast<int64_t*>(ws + L.sums);
+
+    expand_rows_kernel<<<grid_cap(M * 32, 256), 256, 0, s>>>(A_rowptr, M, row_of);
+    int bits = 1;
+    while (bits < 31 && ((int64_t)1 << bits) < K) ++bits;
+    const int passes = (bits + 7) / 8;
+    const int32_t* kin = A_colind;
+    const int32_t* vin = nullptr;   // first pass: value = own index
+    int cur = 0;
+    for (int pass = 0; pass < passes; ++pass) {
+        const int shift = 8 * pass;
+        radix_count_kernel<<<(unsigned)L.ntiles, kSortThreads, 0, s>>>(kin, nnz, shift, L.ntiles, counts);
+        scan_block_sums_kernel<<<(unsigned)L.scan_blocks, 1024, 0, s>>>(counts, L.ncounts, L.per_block, sums);
+        scan_sums_serial_kernel<<<1, 32, 0, s>>>(sums, L.scan_blocks);
+        scan_apply_kernel<<<(unsigned)L.scan_blocks, 1024, 0, s>>>(counts, L.ncounts, L.per_block, sums);
+        radix_scatter_kernel<<<(unsigned)L.ntiles, kSortThreads, 0, s>>>(kin, vin, nnz, shift, L.ntiles,
+                                                                          counts, kb[cur], vb[cur]);
+        kin = kb[cur];
+        vin = vb[cur];
+        cur ^= 1;
+    }
+    colptr_kernel<<<grid_cap(K + 1, 256), 256, 0, s>>>(kin, nnz, K, out_colptr);
+    const unsigned g = grid_cap(nnz, 256);
+    switch (out_vals ? elem_bytes(val_dtype) : 4) {
+        case 4: finish_kernel<int32_t><<<g, 256, 0, s>>>(vin, row_of, (const int32_t*)A_vals, nnz, out_rowind, (int32_t*)out_vals, out_perm); break;
+        case 2: finish_kernel<uint16_t><<<g, 256, 0, s>>>(vin, row_of, (const uint16_t*)A_vals, nnz, out_rowind, (uint16_t*)out_vals, out_perm); break;
+        default: finish_kernel<uint8_t><<<g, 256, 0, s>>>(vin, row_of, (const uint8_t*)A_vals, nnz, out_rowind, (uint8_t*)out_vals, out_perm); break;
+    }
+    return cudaGetLastError() == cudaSuccess ? SPMM_OK : SPMM_ERR_CUDA;
+}
