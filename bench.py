@@ -92,7 +92,7 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
+    def __init__(self, index):
         self.index = index
         self.proc = None
         self.out = []
@@ -100,8 +100,9 @@ class ClockSampler:
 
     def start(self):
         try:
+            sel = [f"--id={self.index}"] if self.index else []
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                ["nvidia-smi", *sel, f"--query-gpu={self.Q}",
                  "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             time.sleep(0.6)
@@ -236,10 +237,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     assert binding.spmm_get_device_status(ws) == 0
 
-    try:
-        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
-    except Exception:
-        gpu_id = str(local)
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
+    gpu_id = vis[local].strip() if local < len(vis) and vis[local].strip() else None
     sampler = ClockSampler(gpu_id)
     sampler.start()
     if world > 1:

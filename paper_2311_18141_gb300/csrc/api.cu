@@ -246,13 +246,14 @@ int spmm_csr(const int32_t* A_rowptr, const int32_t* A_colind, const void* A_val
         RB = (int32_t)((M + TR - 1) / TR);
         D = plan_default_chunk(M, nnz, TC, device_sm_count());
         cap = plan_chunk_cap(M, nnz, TR, D);
+        // layout [scratch: status, counters, slots][plan arrays]: the status
+        // word stays at the start of the caller's workspace
         const size_t pb = plan_array_bytes(TR, cap);
         const Scratch sc = scratch_layout(TR, TC, cap, N);
         if (workspace_bytes < pb + sc.total) return SPMM_ERR_WORKSPACE;
-        plan_carve(ws, TR, cap, &blk_base, &bnd_row, &bnd_nnz);
+        plan_carve(ws + sc.total, TR, cap, &blk_base, &bnd_row, &bnd_nnz);
         if (plan_build(A_rowptr, M, TR, RB, D, cap, blk_base, bnd_row, bnd_nnz, s) != cudaSuccess)
             return SPMM_ERR_CUDA;
-        ws += pb;
         workspace_bytes -= pb;
     }
     const Scratch sc = scratch_layout(TR, TC, cap, N);

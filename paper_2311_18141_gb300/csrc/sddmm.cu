@@ -243,12 +243,12 @@ extern "C" int spmm_sddmm_csr(const int32_t* A_rowptr, const int32_t* A_colind, 
         RB = (int32_t)M;
         D = plan_default_chunk(M, nnz, 1, device_sm_count());
         cap = plan_chunk_cap(M, nnz, TR, D);
+        // layout [status, counter (256 B)][plan arrays]
         const size_t pb = plan_array_bytes(TR, cap);
-        if (workspace_bytes < pb + kStatusBytes + 256) return SPMM_ERR_WORKSPACE;
-        plan_carve(ws, TR, cap, &blk_base, &bnd_row, &bnd_nnz);
+        if (workspace_bytes < pb + 256) return SPMM_ERR_WORKSPACE;
+        plan_carve(ws + 256, TR, cap, &blk_base, &bnd_row, &bnd_nnz);
         if (plan_build(A_rowptr, M, TR, RB, D, cap, blk_base, bnd_row, bnd_nnz, st) != cudaSuccess)
             return SPMM_ERR_CUDA;
-        ws += pb;
         workspace_bytes -= pb;
     }
     const size_t need = kStatusBytes + 4 * (size_t)TR;

@@ -243,7 +243,9 @@ __device__ __forceinline__ void process_unit(const Problem& p, int i, int j, int
             piece = carried || head;
             tail = carried && !head;
         }
-        const bool is_long = valid && (piece || L > K::SHORT_MAX);
+        // with one group per warp there is no short path: every row (empty
+        // ones included, which still write C) is walked by the whole warp
+        const bool is_long = valid && (piece || L > K::SHORT_MAX || K::SHORT_MAX == 0);
         const bool is_short = valid && !is_long;
 
         // ---- long rows and split rows: the whole warp per row ----

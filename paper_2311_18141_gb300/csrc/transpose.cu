@@ -235,7 +235,8 @@ extern "C" int spmm_csr_transpose(const int32_t* A_rowptr, const int32_t* A_coli
     if (K >= ((int64_t)1 << 31) - 1) return SPMM_ERR_INVALID_ARG;
     if (!A_rowptr || !out_colptr || (nnz > 0 && (!A_colind || !out_rowind)))
         return SPMM_ERR_INVALID_ARG;
-    if (out_vals && (!A_vals || elem_bytes(val_dtype) == 0)) return SPMM_ERR_INVALID_ARG;
+    if (out_vals && elem_bytes(val_dtype) == 0) return SPMM_ERR_UNSUPPORTED;
+    if (nnz > 0 && out_vals && !A_vals) return SPMM_ERR_INVALID_ARG;
     const TransposeLayout L = transpose_layout(nnz);
     if (!workspace || workspace_bytes < L.total || ((uintptr_t)workspace & 255u))
         return SPMM_ERR_WORKSPACE;
