@@ -99,26 +99,42 @@ class ClockSampler:
         self.t0 = self.t1 = None
 
     def start(self):
+        """Start sampling and wait for the first sample, so that nvidia-smi's
+        own start-up is over before the timed region begins."""
+        import threading
         try:
             sel = [f"--id={self.index}"] if self.index else []
             self.proc = subprocess.Popen(
                 ["nvidia-smi", *sel, f"--query-gpu={self.Q}",
                  "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            time.sleep(0.6)
         except OSError:
             self.proc = None
+            return
+        self.lines = []
+        first = threading.Event()
+
+        def reader():
+            for line in self.proc.stdout:
+                self.lines.append(line)
+                first.set()
+        self.thread = threading.Thread(target=reader, daemon=True)
+        self.thread.start()
+        first.wait(timeout=10.0)
+        time.sleep(0.3)
+        self.skip = len(self.lines)   # samples taken before the timed region
 
     def stop(self):
         if self.proc is None:
             return
+        timed = self.lines[self.skip:]
         self.proc.terminate()
         try:
-            out, _ = self.proc.communicate(timeout=5)
+            self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-            out, _ = self.proc.communicate()
-        self.out = [l.split(",") for l in out.strip().splitlines() if l.count(",") >= 8]
+        use = timed if timed else self.lines
+        self.out = [l.split(",") for l in use if l.count(",") >= 8]
 
     def summary(self):
         if not self.out:
@@ -325,7 +341,8 @@ def run_ours(args):
                          "peak_source": f"{peak_kind} (copy bandwidth)",
                          "algorithmic_bytes_per_launch": algo_bytes,
                          "kernel": "spmm_csr_persistent<TagF32,8,1>",
-                         "launch_ms": launch_ms, "kernel_source_sha256_16": src_hash},
+                         "launch_ms": launch_ms, "launch_ms_min": min(per_launch),
+                         "launch_ms_max": max(per_launch), "kernel_source_sha256_16": src_hash},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": args.steps,

@@ -60,7 +60,7 @@ def load_library(path: str | None = None):
     with _lock:
         if _lib is not None:
             return _lib
-        path = path or LIB_PATH
+        path = path or os.environ.get("SPMM_GB300_LIB") or LIB_PATH
         if not os.path.exists(path):
             raise ImportError(f"CUDA library not built: {path} (run __graft_entry__.build())")
         lib = ctypes.CDLL(path)

@@ -42,9 +42,12 @@ def _stale(out: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
-    os.makedirs(LIBDIR, exist_ok=True)
-    objdir = os.path.join(LIBDIR, "obj")
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None,
+          out_dir: str | None = None) -> str:
+    libdir = out_dir or LIBDIR
+    lib = os.path.join(libdir, "libspmm_gb300.so")
+    os.makedirs(libdir, exist_ok=True)
+    objdir = os.path.join(libdir, "obj")
     os.makedirs(objdir, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers.append(os.path.join(INCLUDE, "spmm_gb300.h"))
@@ -69,15 +72,22 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
         errs = [e for e in ex.map(compile_one, zip(srcs, objs)) if e]
     if errs:
         raise RuntimeError("nvcc failed:\n" + "\n".join(errs))
-    if force or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [cc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n" + r.stderr)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    import argparse
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--force", action="store_true")
+    ap.add_argument("-v", action="store_true")
+    ap.add_argument("--out", default=None, help="output directory (default: _lib)")
+    ap.add_argument("-D", action="append", default=[], help="extra nvcc macro definitions")
+    a = ap.parse_args()
+    print(build(force=a.force, verbose=a.v, extra=[f"-D{d}" for d in a.D], out_dir=a.out))

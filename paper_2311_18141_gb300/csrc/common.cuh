@@ -7,7 +7,7 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
-#include "../../include/spmm_gb300.h"
+#include "spmm_gb300.h"
 
 namespace spmm {
 

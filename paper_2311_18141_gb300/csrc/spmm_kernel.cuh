@@ -26,6 +26,10 @@
 
 #include "common.cuh"
 
+#ifndef SPMM_MINBLOCKS
+#define SPMM_MINBLOCKS 3   // resident 256-thread CTAs per SM the register budget targets
+#endif
+
 namespace spmm {
 
 template <typename Tag, int LPN_, int VPL_>
@@ -36,17 +40,22 @@ struct KCfg {
     static constexpr int G = 32 / LPN;
     static constexpr int NE = VPL * EPV;
     static constexpr int ESZ = 16 / EPV;                       // bytes per B element
-    static constexpr int SHORT_MAX = (G == 1) ? 0 : (LPN > 8 ? LPN : 8);
-    static constexpr int SPL = (SHORT_MAX + LPN - 1) / LPN;    // short-row nnz per sub-lane
     static constexpr int U = (32 / G) < 4 ? (32 / G) : 4;      // steps in flight, long path
-    static constexpr int US = 4;                               // steps in flight, short path
+    // Short rows: SUB lanes per row, each lane VPS vectors (about 16 floats),
+    // RPP rows of a 32-row batch per pass, SUB passes per batch.
+    static constexpr int WF = LPN * VPL * EPV;                 // floats of a column block
+    static constexpr int SUB = (WF / 16) < 1 ? 1 : ((WF / 16) > 32 ? 32 : (WF / 16));
+    static constexpr int VPS = (WF / SUB / EPV) < 1 ? 1 : (WF / SUB / EPV);
+    static constexpr int RPP = 32 / SUB;
+    static constexpr int NS = VPS * EPV;                       // short-path accumulators
+    static constexpr int SHORT_MAX = 16;                       // longer rows: whole warp
 };
 
 // Per-lane view of column block j.
 struct LaneCols {
     const char* b;       // B + first column of this lane's vector 0 (bytes)
     int64_t ldb_bytes;
-    int64_t c_off;       // element offset of this lane's vector 0 within a C row
+    int32_t c_off;       // element offset of this lane's vector 0 within a C row
     uint32_t vmask;      // bit q set when vector q lies inside the column block
 };
 
@@ -65,6 +74,52 @@ __device__ __forceinline__ LaneCols lane_cols(const Problem& p, int j, int sl) {
     for (int q = 0; q < K::VPL; ++q)
         if (c0 + (int64_t)q * K::LPN * K::EPV < col_hi) lc.vmask |= 1u << q;
     return lc;
+}
+
+// Per-lane view of column block j in the short-row layout: sub-lane t of a
+// row owns vectors t, t+SUB, t+2*SUB, ... of the block.
+template <class K>
+__device__ __forceinline__ LaneCols lane_cols_short(const Problem& p, int j, int t) {
+    LaneCols lc;
+    const int64_t col_lo = (int64_t)j * p.W;
+    int64_t col_hi = col_lo + p.W;
+    if (col_hi > p.N) col_hi = p.N;
+    const int64_t c0 = col_lo + (int64_t)t * K::EPV;
+    lc.b = reinterpret_cast<const char*>(p.B) + c0 * K::ESZ;
+    lc.ldb_bytes = p.ldb * K::ESZ;
+    lc.c_off = c0;
+    lc.vmask = 0;
+#pragma unroll
+    for (int v = 0; v < K::VPS; ++v)
+        if (c0 + (int64_t)v * K::SUB * K::EPV < col_hi) lc.vmask |= 1u << v;
+    return lc;
+}
+
+// Short-row store: C[r] = beta*C[r] + scale*acc in the short-row layout.
+template <class K>
+__device__ __forceinline__ void store_row_short(const Problem& p, int64_t r, const float* acc,
+                                                const LaneCols& lc) {
+    float sa = 1.0f;
+    if (p.a_scale) sa = __ldg(p.a_scale + r);
+    float* dst = p.C + r * p.ldc + lc.c_off;
+#pragma unroll
+    for (int v = 0; v < K::VPS; ++v) {
+        if (!((lc.vmask >> v) & 1u)) continue;
+#pragma unroll
+        for (int h = 0; h < K::EPV / 4; ++h) {
+            float* d = dst + v * K::SUB * K::EPV + h * 4;
+            const float* a = acc + v * K::EPV + h * 4;
+            float4 o = make_float4(a[0] * sa, a[1] * sa, a[2] * sa, a[3] * sa);
+            if (p.beta != 0.0f) {
+                const float4 old = __ldcg(reinterpret_cast<const float4*>(d));
+                o.x = fmaf(p.beta, old.x, o.x);
+                o.y = fmaf(p.beta, old.y, o.y);
+                o.z = fmaf(p.beta, old.z, o.z);
+                o.w = fmaf(p.beta, old.w, o.w);
+            }
+            st_cs_f4(d, o);
+        }
+    }
 }
 
 // Write one finished row: C[r] = beta*C[r] + scale*acc (lanes of one group).
@@ -211,9 +266,8 @@ __device__ __forceinline__ void row_warp(const Problem& p, int rs, int L, const 
 // One work unit: chunk c (global gc) of row block i, column block j.
 template <class K, class Tag>
 __device__ __forceinline__ void process_unit(const Problem& p, int i, int j, int c,
-                                             const LaneCols& lc, int lane) {
+                                             const LaneCols& lc, const LaneCols& ls, int lane) {
     const int g = lane / K::LPN;
-    const int sl = lane - g * K::LPN;
     const int gc = p.blk_base[i] + c;
     const int bi = gc + i;
     const int x0 = p.bnd_row[bi], y0 = p.bnd_nnz[bi];
@@ -229,9 +283,13 @@ __device__ __forceinline__ void process_unit(const Problem& p, int i, int j, int
         bool valid = (r <= x1) && (r < row_hi);
         int s = 0, L = 0;
         bool piece = false, tail = false;
+        // rowptr[r] by this lane, rowptr[r+1] from the next lane (lane 31 loads it)
+        const int rp_here = (r <= x1 && r < row_hi) ? __ldg(p.rowptr + r) : 0;
+        int rp_next = __shfl_down_sync(kFull, rp_here, 1);
+        if (lane == 31 && r < x1 && r < row_hi) rp_next = __ldg(p.rowptr + r + 1);
         if (valid) {
-            const int rstart = __ldg(p.rowptr + r);
-            const int rend = (r < x1) ? __ldg(p.rowptr + r + 1) : y1;
+            const int rstart = rp_here;
+            const int rend = (r < x1) ? rp_next : y1;
             const bool carried = rstart < y0;
             const bool head = (r == x1);
             s = max(rstart, y0);
@@ -243,10 +301,8 @@ __device__ __forceinline__ void process_unit(const Problem& p, int i, int j, int
             piece = carried || head;
             tail = carried && !head;
         }
-        // with one group per warp there is no short path: every row (empty
-        // ones included, which still write C) is walked by the whole warp
-        const bool is_long = valid && (piece || L > K::SHORT_MAX || K::SHORT_MAX == 0);
-        const bool is_short = valid && !is_long;
+        const bool is_long = valid && (piece || L > K::SHORT_MAX);
+        const bool is_short = valid && !is_long;   // empty rows included
 
         // ---- long rows and split rows: the whole warp per row ----
         unsigned lmask = __ballot_sync(kFull, is_long);
@@ -266,62 +322,42 @@ __device__ __forceinline__ void process_unit(const Problem& p, int i, int j, int
             }
         }
 
-        // ---- short rows: one row per group ----
-        if constexpr (K::SHORT_MAX > 0) {
-            const unsigned smask = __ballot_sync(kFull, is_short);
-            const int nshort = __popc(smask);
-            for (int q0 = 0; q0 < nshort; q0 += K::G) {
-                const int q = q0 + g;
-                const bool act = q < nshort;
-                const int pos = act ? nth_set_bit(smask, q) : 0;
-                const int rs = __shfl_sync(kFull, s, pos);
-                int rl = __shfl_sync(kFull, L, pos);
-                if (!act) rl = 0;
-                int colr[K::SPL];
-                float valr[K::SPL];
+        // ---- short rows: SUB lanes per row, RPP rows per pass ----
+        const unsigned smask = __ballot_sync(kFull, is_short);
+        if (smask) {
+            const int t = lane % K::SUB;
+#pragma unroll 1
+            for (int pass = 0; pass < K::SUB; ++pass) {
+                const unsigned pbits =
+                    K::RPP == 32 ? smask : ((smask >> (pass * K::RPP)) & ((1u << K::RPP) - 1u));
+                if (!pbits) continue;
+                const int q = pass * K::RPP + lane / K::SUB;   // row slot of this lane
+                const int rs = __shfl_sync(kFull, s, q);
+                int rl = __shfl_sync(kFull, L, q);
+                const bool mine = (smask >> q) & 1u;
+                if (!mine) rl = 0;
+                const int lmax = __reduce_max_sync(kFull, rl);
+                float acc[K::NS];
 #pragma unroll
-                for (int u = 0; u < K::SPL; ++u) {
-                    const int idx = sl + u * K::LPN;
-                    colr[u] = 0;
-                    valr[u] = 0.0f;
-                    if (idx < rl) {
-                        colr[u] = ld_stream_i32(p.colind + rs + idx);
-                        valr[u] = load_aval(p.vals, p.a_dtype, (int64_t)rs + idx);
-                        if (p.b_scale) valr[u] *= __ldg(p.b_scale + colr[u]);
+                for (int e = 0; e < K::NS; ++e) acc[e] = 0.0f;
+                for (int k = 0; k < lmax; ++k) {
+                    if (k < rl) {
+                        const int c0 = __ldg(p.colind + rs + k);
+                        float a0 = load_aval(p.vals, p.a_dtype, (int64_t)rs + k);
+                        if (p.b_scale) a0 *= __ldg(p.b_scale + c0);
+                        uint4 b0[K::VPS];
+                        const char* r0 = ls.b + (int64_t)c0 * ls.ldb_bytes;
+#pragma unroll
+                        for (int v = 0; v < K::VPS; ++v)
+                            if ((ls.vmask >> v) & 1u) b0[v] = ld_b16(r0 + v * K::SUB * 16);
+#pragma unroll
+                        for (int v = 0; v < K::VPS; ++v)
+                            if ((ls.vmask >> v) & 1u) fma_vec<Tag>(acc + v * K::EPV, a0, b0[v]);
                     }
                 }
-                const int tmax = __reduce_max_sync(kFull, rl);
-                float acc[K::NE];
-#pragma unroll
-                for (int e = 0; e < K::NE; ++e) acc[e] = 0.0f;
-#pragma unroll
-                for (int t0 = 0; t0 < K::SHORT_MAX; t0 += K::US) {
-                    if (t0 >= tmax) break;
-                    uint4 bv[K::US][K::VPL];
-                    float av[K::US];
-#pragma unroll
-                    for (int u = 0; u < K::US; ++u) {
-                        const int t = t0 + u;
-                        const int srcl = g * K::LPN + (t % K::LPN);
-                        const int cc = __shfl_sync(kFull, colr[t / K::LPN], srcl);
-                        av[u] = __shfl_sync(kFull, valr[t / K::LPN], srcl);
-                        const char* rp = lc.b + (int64_t)cc * lc.ldb_bytes;
-#pragma unroll
-                        for (int qq = 0; qq < K::VPL; ++qq)
-                            if (t < rl && ((lc.vmask >> qq) & 1u))
-                                bv[u][qq] = ld_b16(rp + qq * K::LPN * 16);
-                    }
-#pragma unroll
-                    for (int u = 0; u < K::US; ++u) {
-                        if (t0 + u < rl) {
-#pragma unroll
-                            for (int qq = 0; qq < K::VPL; ++qq)
-                                if ((lc.vmask >> qq) & 1u)
-                                    fma_vec<Tag>(acc + qq * K::EPV, av[u], bv[u][qq]);
-                        }
-                    }
-                }
-                if (act) store_row<K>(p, (int64_t)rb + pos, acc, lc);
+                // an empty row with beta == 1 and no row scale leaves C unchanged
+                if (mine && !(rl == 0 && p.beta == 1.0f && p.a_scale == nullptr))
+                    store_row_short<K>(p, (int64_t)rb + q, acc, ls);
             }
         }
     }
@@ -329,7 +365,7 @@ __device__ __forceinline__ void process_unit(const Problem& p, int i, int j, int
 
 // The persistent kernel: each warp is an independent worker.
 template <class Tag, int LPN, int VPL>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, SPMM_MINBLOCKS)
 spmm_csr_persistent(const Problem p, int tile_order) {
     using K = KCfg<Tag, LPN, VPL>;
     const int lane = threadIdx.x & 31;
@@ -353,12 +389,13 @@ spmm_csr_persistent(const Problem p, int tile_order) {
         if (nch == 0) continue;
         if (ld_relaxed(p.tile_ctr + tid) >= nch) continue;
         const LaneCols lc = lane_cols<K>(p, j, sl);
+        const LaneCols ls = lane_cols_short<K>(p, j, lane % K::SUB);
         while (true) {
             int c = 0;
             if (lane == 0) c = atomicAdd(p.tile_ctr + tid, 1);
             c = __shfl_sync(kFull, c, 0);
             if (c >= nch) break;
-            process_unit<K, Tag>(p, i, j, c, lc, lane);
+            process_unit<K, Tag>(p, i, j, c, lc, ls, lane);
         }
     }
 }
