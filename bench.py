@@ -33,7 +33,7 @@ METRIC = "SpMM GFLOP/s (2·nnz·N) and % HBM roofline; BF16 vs FP32 at stated er
 WORKLOAD = "rmat-s22-ef16-n128-fp32-grid16x4"
 FALLBACK_HBM_GBS = 6800.0
 PROFILE = os.path.join(ROOT, "profiles", "spmm_csr_persistent_rmat_s22_n128.md")
-KERNEL_SOURCES = ["common.cuh", "spmm_kernel.cuh", "spmm_launch_impl.cuh", "spmm_f32.cu",
+KERNEL_SOURCES = ["common.cuh", "spmm_kernel.cuh", "spmm_launch_impl.cuh", "spmm_f32_f32.cu",
                   "plan.cu"]
 
 
@@ -75,6 +75,19 @@ def stored_traffic(src_hash: str):
     if not m_hash or not m_traffic or m_hash.group(1) != src_hash:
         return None
     return float(m_traffic.group(1))
+
+
+def kernel_shape(N, TC, epv=4):
+    """(lanes per nonzero, vectors per lane) the library picks for FP32 B."""
+    w = -(-N // TC)
+    w = -(-w // epv) * epv
+    nvec = w // epv
+    if nvec <= 32:
+        lpn = 2
+        while lpn < nvec:
+            lpn *= 2
+        return lpn, 1
+    return 32, 2 if nvec <= 64 else 4
 
 
 def measured_peaks():
@@ -235,6 +248,8 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     binding.load_library()
     TR, TC = (int(x) for x in args.grid.split("x"))
+    if args.order < 0 or args.order > 3:
+        raise SystemExit("--order is 0..3")
     A, B = make_workload(args.scale, args.n, dev)
     M, K, N, nnz = A.M, A.K, args.n, A.nnz
     C = torch.empty(M, N, device=dev)
@@ -340,7 +355,7 @@ def run_ours(args):
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": f"{peak_kind} (copy bandwidth)",
                          "algorithmic_bytes_per_launch": algo_bytes,
-                         "kernel": "spmm_csr_persistent<TagF32,8,1>",
+                         "kernel": "spmm_csr_persistent<TagF32,TagF32,%d,%d>" % kernel_shape(N, TC),
                          "launch_ms": launch_ms, "launch_ms_min": min(per_launch),
                          "launch_ms_max": max(per_launch), "kernel_source_sha256_16": src_hash},
             "cpu_baseline": cpu,

@@ -71,7 +71,8 @@ typedef struct spmm_tuning {
     int32_t chunk_items;   /* merge-path items (rows + nonzeros) per work unit        */
     int32_t warps_per_cta; /* 4 or 8                                                  */
     int32_t ctas_per_sm;   /* persistent CTAs per SM; 0 = as many as fit              */
-    int32_t tile_order;    /* 0: steal along the tile row first, 1: along the column   */
+    int32_t tile_order;    /* bit 0: steal along the tile column first (else the row);
+                              bit 1: stagger home tiles per warp (else per CTA)       */
     int32_t reserved[4];
 } spmm_tuning;
 

@@ -61,7 +61,7 @@ void resolve_tuning(const spmm_tuning* in, spmm_tuning* out) {
     if (in) *out = *in;
     if (out->warps_per_cta != 4 && out->warps_per_cta != 8) out->warps_per_cta = 8;
     if (out->ctas_per_sm < 0) out->ctas_per_sm = 0;
-    if (out->tile_order != 1) out->tile_order = 0;
+    if (out->tile_order < 0 || out->tile_order > 3) out->tile_order = 0;
     if (out->chunk_items < 0) out->chunk_items = 0;
 }
 
@@ -274,15 +274,11 @@ int spmm_csr(const int32_t* A_rowptr, const int32_t* A_colind, const void* A_val
     LaunchOpts o;
     o.warps_per_cta = tun.warps_per_cta;
     o.ctas_per_sm = tun.ctas_per_sm;
-    o.tile_order = tun.tile_order;
+    o.flags = tun.tile_order;
     o.units = cap * TC;
-    cudaError_t e;
-    switch (b_dtype) {
-        case SPMM_F32: e = launch_spmm_f32(lpn, vpl, p, o, s); break;
-        case SPMM_F16: e = launch_spmm_f16(lpn, vpl, p, o, s); break;
-        case SPMM_BF16: e = launch_spmm_bf16(lpn, vpl, p, o, s); break;
-        default: e = launch_spmm_e4m3(lpn, vpl, p, o, s); break;
-    }
+    const LaunchFn fn = spmm_launcher(a_dtype, b_dtype);
+    if (!fn) return SPMM_ERR_UNSUPPORTED;
+    const cudaError_t e = fn(lpn, vpl, p, o, s);
     return e == cudaSuccess ? SPMM_OK : SPMM_ERR_CUDA;
 }
 

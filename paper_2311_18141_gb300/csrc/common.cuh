@@ -60,26 +60,18 @@ __device__ __forceinline__ void st_cg_f4(float* p, float4 v) {
 
 // ---------------------------------------------------------------- math ----
 
-// acc[0..1] += a * b[0..1] as one packed FP32 FMA (fma.rn.f32x2, sm_100+).
-__device__ __forceinline__ void ffma2(float& c0, float& c1, float a, float b0, float b1) {
-#if defined(SPMM_USE_FFMA2) && defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000)
-    asm("{\n\t.reg .b64 ra, rb, rc;\n\t"
-        "mov.b64 ra, {%2, %2};\n\t"
-        "mov.b64 rb, {%3, %4};\n\t"
-        "mov.b64 rc, {%0, %1};\n\t"
-        "fma.rn.f32x2 rc, ra, rb, rc;\n\t"
-        "mov.b64 {%0, %1}, rc;\n\t}"
-        : "+f"(c0), "+f"(c1)
-        : "f"(a), "f"(b0), "f"(b1));
+// c += a * b on two FP32 lanes at once (packed FFMA2 on sm_100 and later).
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000)
+    return __ffma2_rn(a, b, c);
 #else
-    c0 = fmaf(a, b0, c0);
-    c1 = fmaf(a, b1, c1);
+    return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
 #endif
 }
 
 // -------------------------------------------------------------- decode ----
 
-// Element traits of B's storage type: EPV = elements per 16-byte vector.
+// Element traits of a storage type: EPV = elements per 16-byte vector.
 struct TagF32 { static constexpr int EPV = 4;  static constexpr int dtype = SPMM_F32; };
 struct TagF16 { static constexpr int EPV = 8;  static constexpr int dtype = SPMM_F16; };
 struct TagBF16 { static constexpr int EPV = 8; static constexpr int dtype = SPMM_BF16; };
@@ -100,60 +92,66 @@ __device__ __forceinline__ float2 e4m3x2_to_f2(uint16_t w) {
     return h2f2(h2);
 }
 
-// acc[0..EPV) += a * decode(v)
+// acc[0 .. EPV/2) += a2 * decode(v), a2 = (a, a)
 template <typename Tag>
-__device__ __forceinline__ void fma_vec(float* acc, float a, const uint4& v);
+__device__ __forceinline__ void fma_vec(float2* acc, float2 a2, const uint4& v);
 
 template <>
-__device__ __forceinline__ void fma_vec<TagF32>(float* acc, float a, const uint4& v) {
-    ffma2(acc[0], acc[1], a, __uint_as_float(v.x), __uint_as_float(v.y));
-    ffma2(acc[2], acc[3], a, __uint_as_float(v.z), __uint_as_float(v.w));
+__device__ __forceinline__ void fma_vec<TagF32>(float2* acc, float2 a2, const uint4& v) {
+    acc[0] = ffma2(a2, make_float2(__uint_as_float(v.x), __uint_as_float(v.y)), acc[0]);
+    acc[1] = ffma2(a2, make_float2(__uint_as_float(v.z), __uint_as_float(v.w)), acc[1]);
 }
 template <>
-__device__ __forceinline__ void fma_vec<TagBF16>(float* acc, float a, const uint4& v) {
-    ffma2(acc[0], acc[1], a, bf16lo(v.x), bf16hi(v.x));
-    ffma2(acc[2], acc[3], a, bf16lo(v.y), bf16hi(v.y));
-    ffma2(acc[4], acc[5], a, bf16lo(v.z), bf16hi(v.z));
-    ffma2(acc[6], acc[7], a, bf16lo(v.w), bf16hi(v.w));
+__device__ __forceinline__ void fma_vec<TagBF16>(float2* acc, float2 a2, const uint4& v) {
+    acc[0] = ffma2(a2, make_float2(bf16lo(v.x), bf16hi(v.x)), acc[0]);
+    acc[1] = ffma2(a2, make_float2(bf16lo(v.y), bf16hi(v.y)), acc[1]);
+    acc[2] = ffma2(a2, make_float2(bf16lo(v.z), bf16hi(v.z)), acc[2]);
+    acc[3] = ffma2(a2, make_float2(bf16lo(v.w), bf16hi(v.w)), acc[3]);
 }
 template <>
-__device__ __forceinline__ void fma_vec<TagF16>(float* acc, float a, const uint4& v) {
-    float2 f;
-    f = h2f2(v.x); ffma2(acc[0], acc[1], a, f.x, f.y);
-    f = h2f2(v.y); ffma2(acc[2], acc[3], a, f.x, f.y);
-    f = h2f2(v.z); ffma2(acc[4], acc[5], a, f.x, f.y);
-    f = h2f2(v.w); ffma2(acc[6], acc[7], a, f.x, f.y);
+__device__ __forceinline__ void fma_vec<TagF16>(float2* acc, float2 a2, const uint4& v) {
+    acc[0] = ffma2(a2, h2f2(v.x), acc[0]);
+    acc[1] = ffma2(a2, h2f2(v.y), acc[1]);
+    acc[2] = ffma2(a2, h2f2(v.z), acc[2]);
+    acc[3] = ffma2(a2, h2f2(v.w), acc[3]);
 }
 template <>
-__device__ __forceinline__ void fma_vec<TagE4M3>(float* acc, float a, const uint4& v) {
+__device__ __forceinline__ void fma_vec<TagE4M3>(float2* acc, float2 a2, const uint4& v) {
     const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        float2 f0 = e4m3x2_to_f2((uint16_t)(w[q] & 0xffffu));
-        float2 f1 = e4m3x2_to_f2((uint16_t)(w[q] >> 16));
-        ffma2(acc[4 * q + 0], acc[4 * q + 1], a, f0.x, f0.y);
-        ffma2(acc[4 * q + 2], acc[4 * q + 3], a, f1.x, f1.y);
+        acc[2 * q + 0] = ffma2(a2, e4m3x2_to_f2((uint16_t)(w[q] & 0xffffu)), acc[2 * q + 0]);
+        acc[2 * q + 1] = ffma2(a2, e4m3x2_to_f2((uint16_t)(w[q] >> 16)), acc[2 * q + 1]);
     }
 }
 
-// Decode A's value e of runtime type `dt` (uniform across the warp).
-__device__ __forceinline__ float load_aval(const void* vals, int dt, int64_t e) {
-    switch (dt) {
-        case SPMM_F32:
-            return __int_as_float(ld_stream_i32(reinterpret_cast<const int32_t*>(vals) + e));
-        case SPMM_F16: {
-            uint32_t h = ld_stream_u16(reinterpret_cast<const uint16_t*>(vals) + e);
-            return __half2float(__ushort_as_half((unsigned short)h));
-        }
-        case SPMM_BF16: {
-            uint32_t h = ld_stream_u16(reinterpret_cast<const uint16_t*>(vals) + e);
-            return __uint_as_float(h << 16);
-        }
-        default: {
-            uint32_t q = ld_stream_u8(reinterpret_cast<const uint8_t*>(vals) + e);
-            return e4m3x2_to_f2((uint16_t)q).x;
-        }
-    }
+// A's value e of storage type TagA, as FP32.  `stream` skips L1 allocation.
+template <typename TagA, bool stream>
+__device__ __forceinline__ float aval(const void* vals, int64_t e);
+
+template <> __device__ __forceinline__ float aval<TagF32, true>(const void* v, int64_t e) {
+    return __int_as_float(ld_stream_i32(reinterpret_cast<const int32_t*>(v) + e));
+}
+template <> __device__ __forceinline__ float aval<TagF32, false>(const void* v, int64_t e) {
+    return __ldg(reinterpret_cast<const float*>(v) + e);
+}
+template <> __device__ __forceinline__ float aval<TagF16, true>(const void* v, int64_t e) {
+    return __half2float(__ushort_as_half((unsigned short)ld_stream_u16(reinterpret_cast<const uint16_t*>(v) + e)));
+}
+template <> __device__ __forceinline__ float aval<TagF16, false>(const void* v, int64_t e) {
+    return __half2float(__ldg(reinterpret_cast<const __half*>(v) + e));
+}
+template <> __device__ __forceinline__ float aval<TagBF16, true>(const void* v, int64_t e) {
+    return __uint_as_float(ld_stream_u16(reinterpret_cast<const uint16_t*>(v) + e) << 16);
+}
+template <> __device__ __forceinline__ float aval<TagBF16, false>(const void* v, int64_t e) {
+    return __uint_as_float((uint32_t)__ldg(reinterpret_cast<const unsigned short*>(v) + e) << 16);
+}
+template <> __device__ __forceinline__ float aval<TagE4M3, true>(const void* v, int64_t e) {
+    return e4m3x2_to_f2((uint16_t)ld_stream_u8(reinterpret_cast<const uint8_t*>(v) + e)).x;
+}
+template <> __device__ __forceinline__ float aval<TagE4M3, false>(const void* v, int64_t e) {
+    return e4m3x2_to_f2((uint16_t)__ldg(reinterpret_cast<const unsigned char*>(v) + e)).x;
 }
 
 // Position of the q-th (0-based) set bit of m; requires q < popc(m).  Binary

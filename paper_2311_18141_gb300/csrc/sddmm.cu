@@ -46,8 +46,8 @@ struct SddmmProblem {
 };
 
 template <class K>
-__device__ __forceinline__ void load_dc_row(const SddmmProblem& s, int64_t r, const LaneCols& lc,
-                                            float* d) {
+__device__ __forceinline__ void load_dc_row(const SddmmProblem& s, int64_t r,
+                                            const LaneCols<K::VPL>& lc, float* d) {
     const float* src = s.dC + r * s.lddc + lc.c_off;
 #pragma unroll
     for (int q = 0; q < K::VPL; ++q) {
@@ -70,8 +70,8 @@ __device__ __forceinline__ float group_sum(float x) {
 }
 
 template <class K, class Tag>
-__device__ __forceinline__ void sddmm_unit(const SddmmProblem& s, int i, int c, const LaneCols& lc,
-                                           int lane) {
+__device__ __forceinline__ void sddmm_unit(const SddmmProblem& s, int i, int c,
+                                           const LaneCols<K::VPL>& lc, int lane) {
     const Problem& p = s.p;
     const int g = lane / K::LPN;
     const int sl = lane - g * K::LPN;
@@ -108,11 +108,11 @@ __device__ __forceinline__ void sddmm_unit(const SddmmProblem& s, int i, int c, 
                 float part = 0.0f;
                 if (e < rl) {
                     const int col = __ldg(p.colind + rs + e);
-                    const char* rp = lc.b + (int64_t)col * lc.ldb_bytes;
+                    const char* rp = brow(lc, col);
 #pragma unroll
                     for (int q = 0; q < K::VPL; ++q)
                         if ((lc.vmask >> q) & 1u)
-                            part += dot_vec<Tag>(d + q * K::EPV, ld_b16(rp + q * K::LPN * 16));
+                            part += dot_vec<Tag>(d + q * K::EPV, ld_b16(rp + lc.qoff[q]));
                 }
                 part = group_sum<K::LPN>(part);
                 if (e < rl && sl == 0) s.out[rs + e] = part;
@@ -135,11 +135,11 @@ __device__ __forceinline__ void sddmm_unit(const SddmmProblem& s, int i, int c, 
                 float part = 0.0f;
                 if (e < rl) {
                     const int col = __ldg(p.colind + rs + e);
-                    const char* rp = lc.b + (int64_t)col * lc.ldb_bytes;
+                    const char* rp = brow(lc, col);
 #pragma unroll
                     for (int qq = 0; qq < K::VPL; ++qq)
                         if ((lc.vmask >> qq) & 1u)
-                            part += dot_vec<Tag>(d + qq * K::EPV, ld_b16(rp + qq * K::LPN * 16));
+                            part += dot_vec<Tag>(d + qq * K::EPV, ld_b16(rp + lc.qoff[qq]));
                 }
                 part = group_sum<K::LPN>(part);
                 if (e < rl && sl == 0) s.out[rs + e] = part;
@@ -150,13 +150,13 @@ __device__ __forceinline__ void sddmm_unit(const SddmmProblem& s, int i, int c, 
 
 template <class Tag, int LPN, int VPL>
 __global__ void __launch_bounds__(256, 2) sddmm_persistent(const SddmmProblem s) {
-    using K = KCfg<Tag, LPN, VPL>;
+    using K = KCfg<TagF32, Tag, LPN, VPL>;
     const Problem& p = s.p;
     const int lane = threadIdx.x & 31;
     const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int T = p.TR;
     const int home = warp % T;
-    const LaneCols lc = lane_cols<K>(p, 0, lane % K::LPN);
+    const LaneCols<K::VPL> lc = lane_cols<K, K::VPL, K::LPN>(p, 0, lane % K::LPN);
     for (int step = 0; step < T; ++step) {
         int i = home + step;
         if (i >= T) i -= T;

@@ -1,0 +1,4 @@
+// Persistent SpMM kernels: A values F32, B F32.
+#include "spmm_launch_impl.cuh"
+
+SPMM_DEFINE_LAUNCHER(f32, f32, TagF32, TagF32)

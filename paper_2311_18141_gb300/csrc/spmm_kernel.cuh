@@ -17,11 +17,12 @@
 //     tells the unit that finishes last, which sums the partials in chunk
 //     order and writes C.  No atomics touch C and the result is reproducible.
 //
-// Inside a unit a warp is LPN-lane groups (G = 32/LPN of them); a group
-// covers one B row slice of the column block with 16-byte loads (VPL per
-// lane).  Rows with at most SHORT_MAX nonzeros are taken one per group; longer
-// rows and split rows are walked by the whole warp, groups interleaved over the
-// nonzeros, and reduced across groups with shuffles.
+// Inside a unit a warp loads the row pointers of 32 rows at once.  Rows with
+// at most SHORT_MAX nonzeros (empty rows included) are processed SUB lanes
+// per row, all such rows of the batch in parallel, each lane gathering VPS
+// 16-byte vectors of B per nonzero, one nonzero at a time.  Longer rows and split rows are walked by
+// the whole warp: LPN-lane groups interleaved over the nonzeros, U gathers in
+// flight per lane, then a shuffle reduction across the groups.
 #pragma once
 
 #include "common.cuh"
@@ -29,114 +30,97 @@
 #ifndef SPMM_MINBLOCKS
 #define SPMM_MINBLOCKS 3   // resident 256-thread CTAs per SM the register budget targets
 #endif
+#ifndef SPMM_LONG_UNROLL
+#define SPMM_LONG_UNROLL 4 // B gathers in flight per lane on the whole-warp path
+#endif
 
 namespace spmm {
 
-template <typename Tag, int LPN_, int VPL_>
+// Launch flags of the persistent kernel.
+constexpr int kFlagOrderColumn = 1;   // steal along the tile column first
+constexpr int kFlagWarpHome = 2;      // stagger home tiles per warp instead of per CTA
+
+template <typename TA_, typename TB_, int LPN_, int VPL_>
 struct KCfg {
+    using TA = TA_;
+    using TB = TB_;
     static constexpr int LPN = LPN_;
     static constexpr int VPL = VPL_;
-    static constexpr int EPV = Tag::EPV;
+    static constexpr int EPV = TB::EPV;
     static constexpr int G = 32 / LPN;
-    static constexpr int NE = VPL * EPV;
+    static constexpr int NE = VPL * EPV;                       // long-path floats per lane
     static constexpr int ESZ = 16 / EPV;                       // bytes per B element
-    static constexpr int U = (32 / G) < 4 ? (32 / G) : 4;      // steps in flight, long path
+    // gathers in flight per lane on the whole-warp path: up to SPMM_LONG_UNROLL
+    // steps of VPL vectors, never more steps than a 32-nonzero batch has
+    static constexpr int UB0 = SPMM_LONG_UNROLL / VPL < 1 ? 1 : SPMM_LONG_UNROLL / VPL;
+    static constexpr int UB = (32 / G) < UB0 ? (32 / G) : UB0;
     // Short rows: SUB lanes per row, each lane VPS vectors (about 16 floats),
     // RPP rows of a 32-row batch per pass, SUB passes per batch.
     static constexpr int WF = LPN * VPL * EPV;                 // floats of a column block
     static constexpr int SUB = (WF / 16) < 1 ? 1 : ((WF / 16) > 32 ? 32 : (WF / 16));
     static constexpr int VPS = (WF / SUB / EPV) < 1 ? 1 : (WF / SUB / EPV);
     static constexpr int RPP = 32 / SUB;
-    static constexpr int NS = VPS * EPV;                       // short-path accumulators
+    static constexpr int NS = VPS * EPV;                       // short-path floats per lane
     static constexpr int SHORT_MAX = 16;                       // longer rows: whole warp
 };
 
-// Per-lane view of column block j.
+// Per-lane view of a column block: where this lane's vectors start in a B
+// row and a C row, and which of them fall inside the block.  Vectors outside
+// the block are pointed at the block's first vector, so every gather is to a
+// valid address and needs no predicate; only stores are masked.
+template <int NV>
 struct LaneCols {
-    const char* b;       // B + first column of this lane's vector 0 (bytes)
-    int64_t ldb_bytes;
-    int32_t c_off;       // element offset of this lane's vector 0 within a C row
-    uint32_t vmask;      // bit q set when vector q lies inside the column block
+    const char* b;         // B + this lane's vector 0 (bytes), clamped into the block
+    uint32_t ldb_bytes;    // B row stride in bytes (N <= 2^20, so it fits 32 bits)
+    int32_t c_off;         // element offset of this lane's vector 0 within a C row
+    uint32_t vmask;        // bit q set when vector q lies inside the column block
+    uint32_t qoff[NV];     // byte offset of vector q from b (0 when clamped)
 };
 
-template <class K>
-__device__ __forceinline__ LaneCols lane_cols(const Problem& p, int j, int sl) {
-    LaneCols lc;
-    const int64_t col_lo = (int64_t)j * p.W;
-    int64_t col_hi = col_lo + p.W;
-    if (col_hi > p.N) col_hi = p.N;
-    const int64_t c0 = col_lo + (int64_t)sl * K::EPV;
-    lc.b = reinterpret_cast<const char*>(p.B) + c0 * K::ESZ;
-    lc.ldb_bytes = p.ldb * K::ESZ;
-    lc.c_off = c0;
-    lc.vmask = 0;
-#pragma unroll
-    for (int q = 0; q < K::VPL; ++q)
-        if (c0 + (int64_t)q * K::LPN * K::EPV < col_hi) lc.vmask |= 1u << q;
-    return lc;
-}
-
-// Per-lane view of column block j in the short-row layout: sub-lane t of a
-// row owns vectors t, t+SUB, t+2*SUB, ... of the block.
-template <class K>
-__device__ __forceinline__ LaneCols lane_cols_short(const Problem& p, int j, int t) {
-    LaneCols lc;
+// Lane `t` of a group whose vectors are t, t + STRIDE, t + 2*STRIDE, ...
+template <class K, int NV, int STRIDE>
+__device__ __forceinline__ LaneCols<NV> lane_cols(const Problem& p, int j, int t) {
+    LaneCols<NV> lc;
     const int64_t col_lo = (int64_t)j * p.W;
     int64_t col_hi = col_lo + p.W;
     if (col_hi > p.N) col_hi = p.N;
     const int64_t c0 = col_lo + (int64_t)t * K::EPV;
-    lc.b = reinterpret_cast<const char*>(p.B) + c0 * K::ESZ;
-    lc.ldb_bytes = p.ldb * K::ESZ;
-    lc.c_off = c0;
     lc.vmask = 0;
 #pragma unroll
-    for (int v = 0; v < K::VPS; ++v)
-        if (c0 + (int64_t)v * K::SUB * K::EPV < col_hi) lc.vmask |= 1u << v;
+    for (int q = 0; q < NV; ++q)
+        if (c0 + (int64_t)q * STRIDE * K::EPV < col_hi) lc.vmask |= 1u << q;
+    const int64_t cb = (lc.vmask & 1u) ? c0 : col_lo;
+    lc.b = reinterpret_cast<const char*>(p.B) + cb * K::ESZ;
+    lc.ldb_bytes = (uint32_t)(p.ldb * K::ESZ);
+    lc.c_off = (int32_t)c0;
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+        lc.qoff[q] = ((lc.vmask >> q) & 1u) ? (uint32_t)(q * STRIDE * 16) : 0u;
     return lc;
 }
 
-// Short-row store: C[r] = beta*C[r] + scale*acc in the short-row layout.
-template <class K>
-__device__ __forceinline__ void store_row_short(const Problem& p, int64_t r, const float* acc,
-                                                const LaneCols& lc) {
-    float sa = 1.0f;
-    if (p.a_scale) sa = __ldg(p.a_scale + r);
-    float* dst = p.C + r * p.ldc + lc.c_off;
-#pragma unroll
-    for (int v = 0; v < K::VPS; ++v) {
-        if (!((lc.vmask >> v) & 1u)) continue;
-#pragma unroll
-        for (int h = 0; h < K::EPV / 4; ++h) {
-            float* d = dst + v * K::SUB * K::EPV + h * 4;
-            const float* a = acc + v * K::EPV + h * 4;
-            float4 o = make_float4(a[0] * sa, a[1] * sa, a[2] * sa, a[3] * sa);
-            if (p.beta != 0.0f) {
-                const float4 old = __ldcg(reinterpret_cast<const float4*>(d));
-                o.x = fmaf(p.beta, old.x, o.x);
-                o.y = fmaf(p.beta, old.y, o.y);
-                o.z = fmaf(p.beta, old.z, o.z);
-                o.w = fmaf(p.beta, old.w, o.w);
-            }
-            st_cs_f4(d, o);
-        }
-    }
+// Address of this lane's vector 0 in B row `col`: one 32x32->64 multiply-add.
+template <int NV>
+__device__ __forceinline__ const char* brow(const LaneCols<NV>& lc, int col) {
+    return lc.b + (uint64_t)(uint32_t)col * lc.ldb_bytes;
 }
 
-// Write one finished row: C[r] = beta*C[r] + scale*acc (lanes of one group).
-template <class K>
-__device__ __forceinline__ void store_row(const Problem& p, int64_t r, float* acc,
-                                          const LaneCols& lc) {
+// C[r] = beta*C[r] + scale*acc for the NV vectors of this lane (stride STRIDE).
+template <class K, int NV, int STRIDE>
+__device__ __forceinline__ void store_vecs(const Problem& p, int64_t r, const float2* acc,
+                                           const LaneCols<NV>& lc) {
     float sa = 1.0f;
     if (p.a_scale) sa = __ldg(p.a_scale + r);
     float* dst = p.C + r * p.ldc + lc.c_off;
 #pragma unroll
-    for (int q = 0; q < K::VPL; ++q) {
+    for (int q = 0; q < NV; ++q) {
         if (!((lc.vmask >> q) & 1u)) continue;
 #pragma unroll
         for (int h = 0; h < K::EPV / 4; ++h) {
-            float* d = dst + q * K::LPN * K::EPV + h * 4;
-            const float* a = acc + q * K::EPV + h * 4;
-            float4 o = make_float4(a[0] * sa, a[1] * sa, a[2] * sa, a[3] * sa);
+            float* d = dst + q * STRIDE * K::EPV + h * 4;
+            const float2 lo = acc[q * (K::EPV / 2) + 2 * h];
+            const float2 hi = acc[q * (K::EPV / 2) + 2 * h + 1];
+            float4 o = make_float4(lo.x * sa, lo.y * sa, hi.x * sa, hi.y * sa);
             if (p.beta != 0.0f) {
                 const float4 old = __ldcg(reinterpret_cast<const float4*>(d));
                 o.x = fmaf(p.beta, old.x, o.x);
@@ -154,7 +138,8 @@ __device__ __forceinline__ void store_row(const Problem& p, int64_t r, float* ac
 // whole warp; group 0 holds the vector.
 template <class K>
 __device__ __forceinline__ void piece_row(const Problem& p, int i, int j, int gc, int64_t r,
-                                          bool tail, float* acc, const LaneCols& lc, int lane) {
+                                          bool tail, const float2* acc,
+                                          const LaneCols<K::VPL>& lc, int lane) {
     const int g = lane / K::LPN;
     const int64_t slot = 2 * (int64_t)gc + (tail ? 0 : 1);
     if (g == 0) {
@@ -164,8 +149,9 @@ __device__ __forceinline__ void piece_row(const Problem& p, int i, int j, int gc
             if (!((lc.vmask >> q) & 1u)) continue;
 #pragma unroll
             for (int h = 0; h < K::EPV / 4; ++h) {
-                const float* a = acc + q * K::EPV + h * 4;
-                st_cg_f4(dst + q * K::LPN * K::EPV + h * 4, make_float4(a[0], a[1], a[2], a[3]));
+                const float2 lo = acc[q * (K::EPV / 2) + 2 * h];
+                const float2 hi = acc[q * (K::EPV / 2) + 2 * h + 1];
+                st_cg_f4(dst + q * K::LPN * K::EPV + h * 4, make_float4(lo.x, lo.y, hi.x, hi.y));
             }
         }
         __threadfence();
@@ -193,9 +179,9 @@ __device__ __forceinline__ void piece_row(const Problem& p, int i, int j, int gc
     cb = __shfl_sync(kFull, cb, 0);
     __threadfence();
     if (g != 0) return;
-    float sum[K::NE];
+    float2 sum[K::NE / 2];
 #pragma unroll
-    for (int e = 0; e < K::NE; ++e) sum[e] = 0.0f;
+    for (int e = 0; e < K::NE / 2; ++e) sum[e] = make_float2(0.0f, 0.0f);
     for (int cc = ca; cc <= cb; ++cc) {
         const int64_t s2 = 2 * (int64_t)cc + (cc == cb ? 0 : 1);
         const float* src = p.slots + s2 * p.N + lc.c_off;
@@ -205,54 +191,72 @@ __device__ __forceinline__ void piece_row(const Problem& p, int i, int j, int gc
 #pragma unroll
             for (int h = 0; h < K::EPV / 4; ++h) {
                 const float4 v = ld_cg_f4(src + q * K::LPN * K::EPV + h * 4);
-                float* s = sum + q * K::EPV + h * 4;
-                s[0] += v.x;
-                s[1] += v.y;
-                s[2] += v.z;
-                s[3] += v.w;
+                float2* s = sum + q * (K::EPV / 2) + 2 * h;
+                s[0].x += v.x;
+                s[0].y += v.y;
+                s[1].x += v.z;
+                s[1].y += v.w;
             }
         }
     }
-    store_row<K>(p, r, sum, lc);
+    store_vecs<K, K::VPL, K::LPN>(p, r, sum, lc);
 }
 
 // Whole-warp walk of nonzeros [rs, rs+L) of one row: group g takes nonzeros
-// g, g+G, g+2G, ...; returns the group-summed vector in every group.
-template <class K, class Tag>
-__device__ __forceinline__ void row_warp(const Problem& p, int rs, int L, const LaneCols& lc,
-                                         float* acc, int lane) {
+// g, g+G, g+2G, ...; returns the group-summed vector in every group.  The
+// column indices and values of the next 32 nonzeros are fetched while the
+// current 32 are gathered (Algorithm 2's prefetch of the next tile, at warp
+// scale); UB gathers per lane are in flight before their FMAs.
+template <class K>
+__device__ __forceinline__ void row_warp(const Problem& p, int rs, int L,
+                                         const LaneCols<K::VPL>& lc, float2* acc, int lane) {
     const int g = lane / K::LPN;
 #pragma unroll
-    for (int e = 0; e < K::NE; ++e) acc[e] = 0.0f;
+    for (int e = 0; e < K::NE / 2; ++e) acc[e] = make_float2(0.0f, 0.0f);
+    int col_n = 0;
+    float val_n = 0.0f;
+    if (lane < L) {
+        col_n = ld_stream_i32(p.colind + rs + lane);
+        val_n = aval<typename K::TA, true>(p.vals, (int64_t)rs + lane);
+    }
+#pragma unroll 1
     for (int k = 0; k < L; k += 32) {
         const int cnt = min(32, L - k);
-        int col = 0;
-        float v = 0.0f;
-        if (lane < cnt) {
-            col = ld_stream_i32(p.colind + rs + k + lane);
-            v = load_aval(p.vals, p.a_dtype, (int64_t)rs + k + lane);
-            if (p.b_scale) v *= __ldg(p.b_scale + col);
+        const int col = col_n;
+        float v = val_n;
+        if (p.b_scale && lane < cnt) v *= __ldg(p.b_scale + col);
+        if (k + 32 < L) {
+            const int idx = k + 32 + lane;
+            col_n = 0;
+            val_n = 0.0f;
+            if (idx < L) {
+                col_n = ld_stream_i32(p.colind + rs + idx);
+                val_n = aval<typename K::TA, true>(p.vals, (int64_t)rs + idx);
+            }
         }
-        for (int t = 0; t < cnt; t += K::G * K::U) {
-            uint4 bv[K::U][K::VPL];
-            float av[K::U];
+        const int nsteps = (cnt + K::G - 1) / K::G;
+#pragma unroll 1
+        for (int t0 = 0; t0 < nsteps; t0 += K::UB) {
+            uint4 bv[K::UB][K::VPL];
+            float av[K::UB];
 #pragma unroll
-            for (int u = 0; u < K::U; ++u) {
-                const int src = t + u * K::G + g;
+            for (int u = 0; u < K::UB; ++u) {
+                const int src = (t0 + u) * K::G + g;
                 const int cc = __shfl_sync(kFull, col, src & 31);
                 av[u] = __shfl_sync(kFull, v, src & 31);
-                const char* rp = lc.b + (int64_t)cc * lc.ldb_bytes;
+                const char* rp = brow(lc, cc);
+                if (src < cnt) {
 #pragma unroll
-                for (int q = 0; q < K::VPL; ++q)
-                    if (src < cnt && ((lc.vmask >> q) & 1u))
-                        bv[u][q] = ld_b16(rp + q * K::LPN * 16);
+                    for (int q = 0; q < K::VPL; ++q) bv[u][q] = ld_b16(rp + lc.qoff[q]);
+                }
             }
 #pragma unroll
-            for (int u = 0; u < K::U; ++u) {
-                if (t + u * K::G + g < cnt) {
+            for (int u = 0; u < K::UB; ++u) {
+                if ((t0 + u) * K::G + g < cnt) {
+                    const float2 a2 = make_float2(av[u], av[u]);
 #pragma unroll
                     for (int q = 0; q < K::VPL; ++q)
-                        if ((lc.vmask >> q) & 1u) fma_vec<Tag>(acc + q * K::EPV, av[u], bv[u][q]);
+                        fma_vec<typename K::TB>(acc + q * (K::EPV / 2), a2, bv[u][q]);
                 }
             }
         }
@@ -260,13 +264,68 @@ __device__ __forceinline__ void row_warp(const Problem& p, int rs, int L, const 
 #pragma unroll
     for (int off = K::LPN; off < 32; off <<= 1)
 #pragma unroll
-        for (int e = 0; e < K::NE; ++e) acc[e] += __shfl_xor_sync(kFull, acc[e], off);
+        for (int e = 0; e < K::NE / 2; ++e) {
+            acc[e].x += __shfl_xor_sync(kFull, acc[e].x, off);
+            acc[e].y += __shfl_xor_sync(kFull, acc[e].y, off);
+        }
 }
 
-// One work unit: chunk c (global gc) of row block i, column block j.
-template <class K, class Tag>
+// Short rows of the batch: SUB lanes per row, RPP rows per pass.  Each lane
+// fetches the next nonzero's column and value while gathering the current one.
+template <class K>
+__device__ __forceinline__ void short_rows(const Problem& p, int rb, unsigned smask, int s,
+                                           int L, const LaneCols<K::VPS>& ls, int lane) {
+#pragma unroll 1
+    for (int pass = 0; pass < K::SUB; ++pass) {
+        const unsigned pbits =
+            K::RPP == 32 ? smask : ((smask >> (pass * K::RPP)) & ((1u << K::RPP) - 1u));
+        if (!pbits) continue;
+        const int q = pass * K::RPP + lane / K::SUB;   // row slot of this lane
+        const int rs = __shfl_sync(kFull, s, q);
+        int rl = __shfl_sync(kFull, L, q);
+        const bool mine = (smask >> q) & 1u;
+        if (!mine) rl = 0;
+        const int lmax = __reduce_max_sync(kFull, rl);
+        float2 acc[K::NS / 2];
+#pragma unroll
+        for (int e = 0; e < K::NS / 2; ++e) acc[e] = make_float2(0.0f, 0.0f);
+        int c_n = 0;
+        float a_n = 0.0f;
+        if (rl > 0) {
+            c_n = __ldg(p.colind + rs);
+            a_n = aval<typename K::TA, false>(p.vals, (int64_t)rs);
+        }
+#pragma unroll 1
+        for (int k = 0; k < lmax; ++k) {
+            const int c0 = c_n;
+            float a0 = a_n;
+            if (k + 1 < rl) {
+                c_n = __ldg(p.colind + rs + k + 1);
+                a_n = aval<typename K::TA, false>(p.vals, (int64_t)rs + k + 1);
+            }
+            if (k < rl) {
+                if (p.b_scale) a0 *= __ldg(p.b_scale + c0);
+                const char* r0 = brow(ls, c0);
+                uint4 b0[K::VPS];
+#pragma unroll
+                for (int v = 0; v < K::VPS; ++v) b0[v] = ld_b16(r0 + ls.qoff[v]);
+                const float2 a02 = make_float2(a0, a0);
+#pragma unroll
+                for (int v = 0; v < K::VPS; ++v)
+                    fma_vec<typename K::TB>(acc + v * (K::EPV / 2), a02, b0[v]);
+            }
+        }
+        // an empty row with beta == 1 and no row scale leaves C unchanged
+        if (mine && !(rl == 0 && p.beta == 1.0f && p.a_scale == nullptr))
+            store_vecs<K, K::VPS, K::SUB>(p, (int64_t)rb + q, acc, ls);
+    }
+}
+
+// One work unit: chunk c of row block i, column block j.
+template <class K>
 __device__ __forceinline__ void process_unit(const Problem& p, int i, int j, int c,
-                                             const LaneCols& lc, const LaneCols& ls, int lane) {
+                                             const LaneCols<K::VPL>& lc,
+                                             const LaneCols<K::VPS>& ls, int lane) {
     const int g = lane / K::LPN;
     const int gc = p.blk_base[i] + c;
     const int bi = gc + i;
@@ -281,12 +340,13 @@ __device__ __forceinline__ void process_unit(const Problem& p, int i, int j, int
     for (int rb = x0; rb <= x1 && rb < row_hi; rb += 32) {
         const int r = rb + lane;
         bool valid = (r <= x1) && (r < row_hi);
+        // rowptr[r] by this lane, rowptr[r+1] from the next lane (lane 31 loads
+        // it); r <= x1 <= row_hi <= M, so rowptr[r] exists even for r == row_hi
+        const int rp_here = (r <= x1) ? __ldg(p.rowptr + r) : 0;
+        int rp_next = __shfl_down_sync(kFull, rp_here, 1);
+        if (lane == 31 && r < x1) rp_next = __ldg(p.rowptr + r + 1);
         int s = 0, L = 0;
         bool piece = false, tail = false;
-        // rowptr[r] by this lane, rowptr[r+1] from the next lane (lane 31 loads it)
-        const int rp_here = (r <= x1 && r < row_hi) ? __ldg(p.rowptr + r) : 0;
-        int rp_next = __shfl_down_sync(kFull, rp_here, 1);
-        if (lane == 31 && r < x1 && r < row_hi) rp_next = __ldg(p.rowptr + r + 1);
         if (valid) {
             const int rstart = rp_here;
             const int rend = (r < x1) ? rp_next : y1;
@@ -313,89 +373,53 @@ __device__ __forceinline__ void process_unit(const Problem& p, int i, int j, int
             const int rl = __shfl_sync(kFull, L, src);
             const unsigned flags =
                 __shfl_sync(kFull, (piece ? 1u : 0u) | (tail ? 2u : 0u), src);
-            float acc[K::NE];
-            row_warp<K, Tag>(p, rs, rl, lc, acc, lane);
+            float2 acc[K::NE / 2];
+            row_warp<K>(p, rs, rl, lc, acc, lane);
             if (flags & 1u) {
                 piece_row<K>(p, i, j, gc, (int64_t)rb + src, (flags & 2u) != 0, acc, lc, lane);
             } else if (g == 0) {
-                store_row<K>(p, (int64_t)rb + src, acc, lc);
+                store_vecs<K, K::VPL, K::LPN>(p, (int64_t)rb + src, acc, lc);
             }
         }
 
         // ---- short rows: SUB lanes per row, RPP rows per pass ----
         const unsigned smask = __ballot_sync(kFull, is_short);
-        if (smask) {
-            const int t = lane % K::SUB;
-#pragma unroll 1
-            for (int pass = 0; pass < K::SUB; ++pass) {
-                const unsigned pbits =
-                    K::RPP == 32 ? smask : ((smask >> (pass * K::RPP)) & ((1u << K::RPP) - 1u));
-                if (!pbits) continue;
-                const int q = pass * K::RPP + lane / K::SUB;   // row slot of this lane
-                const int rs = __shfl_sync(kFull, s, q);
-                int rl = __shfl_sync(kFull, L, q);
-                const bool mine = (smask >> q) & 1u;
-                if (!mine) rl = 0;
-                const int lmax = __reduce_max_sync(kFull, rl);
-                float acc[K::NS];
-#pragma unroll
-                for (int e = 0; e < K::NS; ++e) acc[e] = 0.0f;
-                for (int k = 0; k < lmax; ++k) {
-                    if (k < rl) {
-                        const int c0 = __ldg(p.colind + rs + k);
-                        float a0 = load_aval(p.vals, p.a_dtype, (int64_t)rs + k);
-                        if (p.b_scale) a0 *= __ldg(p.b_scale + c0);
-                        uint4 b0[K::VPS];
-                        const char* r0 = ls.b + (int64_t)c0 * ls.ldb_bytes;
-#pragma unroll
-                        for (int v = 0; v < K::VPS; ++v)
-                            if ((ls.vmask >> v) & 1u) b0[v] = ld_b16(r0 + v * K::SUB * 16);
-#pragma unroll
-                        for (int v = 0; v < K::VPS; ++v)
-                            if ((ls.vmask >> v) & 1u) fma_vec<Tag>(acc + v * K::EPV, a0, b0[v]);
-                    }
-                }
-                // an empty row with beta == 1 and no row scale leaves C unchanged
-                if (mine && !(rl == 0 && p.beta == 1.0f && p.a_scale == nullptr))
-                    store_row_short<K>(p, (int64_t)rb + q, acc, ls);
-            }
-        }
+        if (smask) short_rows<K>(p, rb, smask, s, L, ls, lane);
     }
 }
 
 // The persistent kernel: each warp is an independent worker.
-template <class Tag, int LPN, int VPL>
+template <class TA, class TB, int LPN, int VPL>
 __global__ void __launch_bounds__(256, SPMM_MINBLOCKS)
-spmm_csr_persistent(const Problem p, int tile_order) {
-    using K = KCfg<Tag, LPN, VPL>;
+spmm_csr_persistent(const Problem p, int flags) {
+    using K = KCfg<TA, TB, LPN, VPL>;
     const int lane = threadIdx.x & 31;
     const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int T = p.TR * p.TC;
-    const int home = warp % T;
-    const int sl = lane % K::LPN;
+    const int home = ((flags & kFlagWarpHome) ? warp : (int)blockIdx.x) % T;
     for (int step = 0; step < T; ++step) {
         int t = home + step;
         if (t >= T) t -= T;
         int i, j;
-        if (tile_order == 0) {
-            i = t / p.TC;
-            j = t - i * p.TC;
-        } else {
+        if (flags & kFlagOrderColumn) {
             j = t / p.TR;
             i = t - j * p.TR;
+        } else {
+            i = t / p.TC;
+            j = t - i * p.TC;
         }
         const int tid = i * p.TC + j;
         const int nch = p.blk_base[i + 1] - p.blk_base[i];
         if (nch == 0) continue;
         if (ld_relaxed(p.tile_ctr + tid) >= nch) continue;
-        const LaneCols lc = lane_cols<K>(p, j, sl);
-        const LaneCols ls = lane_cols_short<K>(p, j, lane % K::SUB);
+        const LaneCols<K::VPL> lc = lane_cols<K, K::VPL, K::LPN>(p, j, lane % K::LPN);
+        const LaneCols<K::VPS> ls = lane_cols<K, K::VPS, K::SUB>(p, j, lane % K::SUB);
         while (true) {
             int c = 0;
             if (lane == 0) c = atomicAdd(p.tile_ctr + tid, 1);
             c = __shfl_sync(kFull, c, 0);
             if (c >= nch) break;
-            process_unit<K, Tag>(p, i, j, c, lc, ls, lane);
+            process_unit<K>(p, i, j, c, lc, ls, lane);
         }
     }
 }

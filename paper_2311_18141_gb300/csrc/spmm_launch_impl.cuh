@@ -1,4 +1,4 @@
-// Instantiates the persistent SpMM kernel for one B storage type.
+// Instantiates the persistent SpMM kernel for one (A value type, B type).
 #pragma once
 
 #include "launch.cuh"
@@ -6,9 +6,9 @@
 
 namespace spmm {
 
-template <class Tag, int LPN, int VPL>
+template <class TA, class TB, int LPN, int VPL>
 cudaError_t launch_one(const Problem& p, const LaunchOpts& o, cudaStream_t s) {
-    auto kern = spmm_csr_persistent<Tag, LPN, VPL>;
+    auto kern = spmm_csr_persistent<TA, TB, LPN, VPL>;
     const int threads = o.warps_per_cta * 32;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
@@ -19,22 +19,30 @@ cudaError_t launch_one(const Problem& p, const LaunchOpts& o, cudaStream_t s) {
     const int64_t need = (o.units + o.warps_per_cta - 1) / o.warps_per_cta;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    kern<<<(unsigned)grid, threads, 0, s>>>(p, o.tile_order);
+    kern<<<(unsigned)grid, threads, 0, s>>>(p, o.flags);
     return cudaGetLastError();
 }
 
-template <class Tag>
-cudaError_t launch_tag(int lpn, int vpl, const Problem& p, const LaunchOpts& o, cudaStream_t s) {
+template <class TA, class TB>
+cudaError_t launch_pair(int lpn, int vpl, const Problem& p, const LaunchOpts& o, cudaStream_t s) {
     switch (lpn * 10 + vpl) {
-        case 21: return launch_one<Tag, 2, 1>(p, o, s);
-        case 41: return launch_one<Tag, 4, 1>(p, o, s);
-        case 81: return launch_one<Tag, 8, 1>(p, o, s);
-        case 161: return launch_one<Tag, 16, 1>(p, o, s);
-        case 321: return launch_one<Tag, 32, 1>(p, o, s);
-        case 322: return launch_one<Tag, 32, 2>(p, o, s);
-        case 324: return launch_one<Tag, 32, 4>(p, o, s);
+        case 21: return launch_one<TA, TB, 2, 1>(p, o, s);
+        case 41: return launch_one<TA, TB, 4, 1>(p, o, s);
+        case 81: return launch_one<TA, TB, 8, 1>(p, o, s);
+        case 161: return launch_one<TA, TB, 16, 1>(p, o, s);
+        case 321: return launch_one<TA, TB, 32, 1>(p, o, s);
+        case 322: return launch_one<TA, TB, 32, 2>(p, o, s);
+        case 324: return launch_one<TA, TB, 32, 4>(p, o, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
 }  // namespace spmm
+
+#define SPMM_DEFINE_LAUNCHER(a, b, TA, TB)                                               \
+    namespace spmm {                                                                      \
+    cudaError_t launch_spmm_##a##_##b(int lpn, int vpl, const Problem& p,                \
+                                      const LaunchOpts& o, cudaStream_t s) {              \
+        return launch_pair<TA, TB>(lpn, vpl, p, o, s);                                    \
+    }                                                                                     \
+    }
