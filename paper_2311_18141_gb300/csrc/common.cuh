@@ -45,6 +45,14 @@ __device__ __forceinline__ int32_t ld_relaxed(const int32_t* p) {
     return v;
 }
 
+// GPU-scope fetch-and-add with acquire-release semantics.
+__device__ __forceinline__ int atom_add_acq_rel(int* p, int v) {
+    int old;
+    asm volatile("atom.add.acq_rel.gpu.global.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v)
+                 : "memory");
+    return old;
+}
+
 // 16-byte L2 (coherent) load, used to read partial rows written by other SMs.
 __device__ __forceinline__ float4 ld_cg_f4(const float* p) {
     return __ldcg(reinterpret_cast<const float4*>(p));

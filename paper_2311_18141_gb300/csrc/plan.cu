@@ -5,9 +5,11 @@
 // end), items = rows + nonzeros.  Chunk c of the block covers path steps
 // [c*D, (c+1)*D).  Boundary c is the path coordinate (x rows finished,
 // y nonzeros consumed) with x + y = c*D; the step at diagonal x + rowend(x)
-// finishes row x.  The search is the merge-path partition of Merrill and
-// Garland (SC'16) applied per block; it balances work the way Section 1 of
-// the paper asks of a schedule under skewed (R-MAT) row lengths.
+// finishes row x.  Boundaries that would cut a light row are moved to its
+// start, so a row is split between chunks only when it is heavy.  The search
+// is the merge-path partition of Merrill and Garland (SC'16) applied per
+// block; it balances work the way Section 1 of the paper asks of a schedule
+// under skewed (R-MAT) row lengths.
 #include "common.cuh"
 #include "plan.cuh"
 
@@ -83,8 +85,18 @@ __global__ void plan_bounds_kernel(const int32_t* __restrict__ rowptr, int M, in
         if (rowend <= d - mid - 1) xl = mid + 1;
         else xh = mid;
     }
+    // A boundary inside a light row (fewer than D/2 items) moves to that row's
+    // start, so only heavy rows are ever cut between chunks.  The moved
+    // boundary stays on the merge path, moves back by less than D/2, and
+    // boundaries inside heavy rows stay on exact diagonals.
+    int64_t y = d - xl;
+    if (xl < R) {
+        const int64_t rs = (int64_t)rowptr[row_lo + xl] - nnz_lo;
+        const int64_t re = (int64_t)rowptr[row_lo + xl + 1] - nnz_lo;
+        if (y > rs && 2 * (re - rs + 1) < D) y = rs;
+    }
     bnd_row[b] = (int32_t)(row_lo + xl);
-    bnd_nnz[b] = (int32_t)(nnz_lo + (d - xl));
+    bnd_nnz[b] = (int32_t)(nnz_lo + y);
 }
 
 static int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

@@ -154,8 +154,10 @@ __device__ __forceinline__ void piece_row(const Problem& p, int i, int j, int gc
                 st_cg_f4(dst + q * K::LPN * K::EPV + h * 4, make_float4(lo.x, lo.y, hi.x, hi.y));
             }
         }
-        __threadfence();
     }
+    // __syncwarp orders the group's slot stores before lane 0's release; the
+    // acq_rel atomic publishes them and, for the last piece, acquires the
+    // other pieces' stores, which __syncwarp then extends to the whole group.
     __syncwarp();
     int ca = 0, cb = 0, last = 0;
     if (lane == 0) {
@@ -167,8 +169,7 @@ __device__ __forceinline__ void piece_row(const Problem& p, int i, int j, int gc
         cb = (int)(((int64_t)(r - row_lo) + (rend - nnz_lo)) / p.D);
         const int base = p.blk_base[i];
         int* cnt = p.piece_cnt + (int64_t)(base + cb) * p.TC + j;
-        __threadfence();
-        const int old = atomicAdd(cnt, 1);
+        const int old = atom_add_acq_rel(cnt, 1);
         last = (old == cb - ca);
         ca += base;
         cb += base;
@@ -177,7 +178,6 @@ __device__ __forceinline__ void piece_row(const Problem& p, int i, int j, int gc
     if (!last) return;
     ca = __shfl_sync(kFull, ca, 0);
     cb = __shfl_sync(kFull, cb, 0);
-    __threadfence();
     if (g != 0) return;
     float2 sum[K::NE / 2];
 #pragma unroll
