@@ -149,6 +149,32 @@ int spmm_csr(const int32_t* A_rowptr, const int32_t* A_colind, const void* A_val
              void* stream);
 
 /*
+ * spmm_csr_noalloc -- spmm_csr for callers that cannot allocate device memory.
+ *   The paper has no counterpart: this is a library convenience.  Some callers
+ *   cannot call cudaMalloc where they need the product (code inside a memory
+ *   pool they do not own, plug-ins whose host forbids device allocation, paths
+ *   that must not synchronise the device, which cudaMalloc/cudaFree can do).
+ *   This call takes no plan and no workspace: it builds the plan and keeps its
+ *   counters and partial rows in one fixed 16 MiB device array that every GPU
+ *   loading this library holds until the process exits.  It computes the same
+ *   C = beta*C + diag(A_row_scale) * A * (diag(B_row_scale) * B) as spmm_csr
+ *   with plan == NULL; all other arguments are as there.
+ *   It allocates nothing (no cudaMalloc, cudaFree or allocating library call).
+ *   Problems whose spmm_csr_workspace_size exceeds 16 MiB are rejected with
+ *   SPMM_ERR_WORKSPACE before any device work.  The first call on a device
+ *   looks up the array's device address (cudaGetSymbolAddress) with that
+ *   device current; make that first call before any stream capture.  All
+ *   calls on a device share the one array, so calls that overlap on the GPU
+ *   (other streams, other host threads) race and give wrong results: order
+ *   them on one stream or synchronise between them.
+ */
+int spmm_csr_noalloc(const int32_t* A_rowptr, const int32_t* A_colind, const void* A_vals,
+                     int32_t a_dtype, const float* A_row_scale, const void* B, int32_t b_dtype,
+                     const float* B_row_scale, int64_t ldb, float* C, int64_t ldc, int64_t M,
+                     int64_t K, int64_t N, int64_t nnz, int32_t tile_rows, int32_t tile_cols,
+                     float beta, void* stream);
+
+/*
  * spmm_csr_validate -- check the CSR invariants listed above on the device.
  *   Writes SPMM_OK or SPMM_ERR_BAD_CSR into the workspace status word (the
  *   first 64 bytes of `workspace`, which must hold at least 64 bytes); read it

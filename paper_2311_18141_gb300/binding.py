@@ -35,6 +35,7 @@ EXPORTED = [
     "spmm_plan_workspace_size", "spmm_plan_units", "spmm_csr_workspace_size", "spmm_csr",
     "spmm_csr_validate", "spmm_get_device_status", "spmm_csr_transpose_workspace_size",
     "spmm_csr_transpose", "spmm_gather_values", "spmm_sddmm_csr", "spmm_quantize_rows",
+    "spmm_csr_noalloc",
 ]
 
 
@@ -87,6 +88,8 @@ def load_library(path: str | None = None):
         lib.spmm_sddmm_csr.argtypes = [vp, vp, vp, i64, vp, i32, i64, vp, i64, i64, i64, i64, vp,
                                        vp, sz, vp]
         lib.spmm_quantize_rows.argtypes = [vp, i64, i64, i64, i32, vp, i64, vp, vp]
+        lib.spmm_csr_noalloc.argtypes = [vp, vp, vp, i32, vp, vp, i32, vp, i64, vp, i64, i64, i64,
+                                         i64, i64, i32, i32, f32, vp]
         for name in EXPORTED:
             if name not in ("spmm_status_string",):
                 getattr(lib, name).restype = ctypes.c_int
@@ -202,6 +205,16 @@ def spmm_csr(rowptr, colind, vals, B, C, M, K, N, nnz, *, a_scale=None, b_scale=
                         _ptr(C), int(ldc), int(M), int(K), int(N), int(nnz), int(tile_rows),
                         int(tile_cols), float(beta), plan.handle if plan is not None else None,
                         _ptr(ws), int(ws_bytes), _stream(stream)), "spmm_csr")
+
+
+def spmm_csr_noalloc(rowptr, colind, vals, B, C, M, K, N, nnz, *, a_scale=None, b_scale=None,
+                     tile_rows=1, tile_cols=1, beta=0.0, stream=None) -> None:
+    """spmm_csr without a workspace (the library's fixed device scratch array)."""
+    _check(load_library().spmm_csr_noalloc(
+        _ptr(rowptr), _ptr(colind), _ptr(vals), dtype_code(vals.dtype), _ptr(a_scale), _ptr(B),
+        dtype_code(B.dtype), _ptr(b_scale), int(B.stride(0)), _ptr(C), int(C.stride(0)), int(M),
+        int(K), int(N), int(nnz), int(tile_rows), int(tile_cols), float(beta), _stream(stream)),
+        "spmm_csr_noalloc")
 
 
 def spmm_csr_validate(rowptr, colind, M, K, nnz, ws, stream=None) -> None:
