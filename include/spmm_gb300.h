@@ -148,6 +148,72 @@ int spmm_csr(const int32_t* A_rowptr, const int32_t* A_colind, const void* A_val
              float beta, spmm_plan plan, void* workspace, size_t workspace_bytes,
              void* stream);
 
+/* ---------------- batched products ---------------- */
+
+/* One product of a batch: C = beta*C + diag(a_scale) * A * (diag(b_scale) * B).
+ * All pointers are device pointers owned by the caller; layout and alignment
+ * rules are those of spmm_csr.  tile_rows, tile_cols and chunk_items of 0 let
+ * the library choose (tile_cols grows until one column block fits a warp). */
+typedef struct spmm_problem {
+    const int32_t* rowptr;
+    const int32_t* colind;
+    const void* vals;
+    const float* a_scale;      /* nullable */
+    const void* B;
+    const float* b_scale;      /* nullable */
+    float* C;
+    int64_t M, K, N, nnz, ldb, ldc;
+    float beta;
+    int32_t tile_rows, tile_cols, chunk_items;
+} spmm_problem;
+
+typedef struct spmm_batch_s* spmm_batch;
+
+/*
+ * spmm_batch_create -- plans for `count` independent products run as one
+ *   persistent launch.  The batch form of Section 3.4's reservation: every
+ *   product keeps its own merge-path plan, its (chunk, column block) units are
+ *   numbered after those of the products before it, and the warps of one grid
+ *   reserve units from a single counter, so warps that finish one product move
+ *   on to any other.  Products run largest first.  All products share A's value
+ *   type `a_dtype` and B's type `b_dtype`.  `problems` is a host array copied at
+ *   creation; the device arrays it points to must stay valid while the batch is
+ *   used.  Allocates device memory for plans and the descriptor table and
+ *   synchronises `stream`.
+ */
+int spmm_batch_create(spmm_batch* batch, const spmm_problem* problems, int32_t count,
+                      int32_t a_dtype, int32_t b_dtype, void* stream);
+int spmm_batch_destroy(spmm_batch batch);
+
+/* Workspace bytes for spmm_csr_batched / spmm_batch_graph_launch under any
+ * shapes spmm_batch_autotune may choose (chunks of at least 512 items, at most
+ * two column blocks, up to 16 row blocks). */
+int spmm_batch_workspace_size(spmm_batch batch, size_t* bytes);
+
+/* Per-product shapes (host arrays of `count`, in the caller's order; an entry
+ * of 0 or a NULL array keeps the current value).  Rebuilds the plans. */
+int spmm_batch_set_shapes(spmm_batch batch, const int32_t* tile_rows, const int32_t* tile_cols,
+                          const int32_t* chunk_items, void* stream);
+int spmm_batch_get_shapes(spmm_batch batch, int32_t* tile_rows, int32_t* tile_cols,
+                          int32_t* chunk_items);
+
+/* All products of the batch in one persistent launch (after one counter-reset
+ * memset).  No allocation; calls sharing a workspace must not overlap. */
+int spmm_csr_batched(spmm_batch batch, void* workspace, size_t workspace_bytes, void* stream);
+
+/* The same work replayed from a CUDA graph: the first call (and the first call
+ * after a shape change or with another workspace) captures the memset and the
+ * launch into a graph held by the batch; later calls only launch that graph. */
+int spmm_batch_graph_launch(spmm_batch batch, void* workspace, size_t workspace_bytes,
+                            void* stream);
+
+/* Choose row blocks {1,4}, column blocks {1,2} and chunk size {512..4096} per
+ * size class (same N, rows below 10k / 50k / above) by coordinate descent,
+ * timing `reps` batched launches per candidate with CUDA events; leaves the
+ * batch planned with the best shapes and returns the best time in *best_ms. */
+int spmm_batch_autotune(spmm_batch batch, void* workspace, size_t workspace_bytes, int32_t reps,
+                        void* stream, float* best_ms);
+
 /*
  * spmm_csr_noalloc -- spmm_csr for callers that cannot allocate device memory.
  *   The paper has no counterpart: this is a library convenience.  Some callers

@@ -35,7 +35,9 @@ EXPORTED = [
     "spmm_plan_workspace_size", "spmm_plan_units", "spmm_csr_workspace_size", "spmm_csr",
     "spmm_csr_validate", "spmm_get_device_status", "spmm_csr_transpose_workspace_size",
     "spmm_csr_transpose", "spmm_gather_values", "spmm_sddmm_csr", "spmm_quantize_rows",
-    "spmm_csr_noalloc",
+    "spmm_csr_noalloc", "spmm_batch_create", "spmm_batch_destroy", "spmm_batch_workspace_size",
+    "spmm_batch_set_shapes", "spmm_batch_get_shapes", "spmm_csr_batched",
+    "spmm_batch_graph_launch", "spmm_batch_autotune",
 ]
 
 
@@ -49,6 +51,16 @@ class spmm_tuning(ctypes.Structure):
     _fields_ = [("chunk_items", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("tile_order", ctypes.c_int32),
                 ("reserved", ctypes.c_int32 * 4)]
+
+
+class spmm_problem(ctypes.Structure):
+    _fields_ = [("rowptr", ctypes.c_void_p), ("colind", ctypes.c_void_p),
+                ("vals", ctypes.c_void_p), ("a_scale", ctypes.c_void_p),
+                ("B", ctypes.c_void_p), ("b_scale", ctypes.c_void_p), ("C", ctypes.c_void_p),
+                ("M", ctypes.c_int64), ("K", ctypes.c_int64), ("N", ctypes.c_int64),
+                ("nnz", ctypes.c_int64), ("ldb", ctypes.c_int64), ("ldc", ctypes.c_int64),
+                ("beta", ctypes.c_float), ("tile_rows", ctypes.c_int32),
+                ("tile_cols", ctypes.c_int32), ("chunk_items", ctypes.c_int32)]
 
 
 _lib = None
@@ -88,6 +100,15 @@ def load_library(path: str | None = None):
         lib.spmm_sddmm_csr.argtypes = [vp, vp, vp, i64, vp, i32, i64, vp, i64, i64, i64, i64, vp,
                                        vp, sz, vp]
         lib.spmm_quantize_rows.argtypes = [vp, i64, i64, i64, i32, vp, i64, vp, vp]
+        P = ctypes.POINTER
+        lib.spmm_batch_create.argtypes = [P(vp), P(spmm_problem), i32, i32, i32, vp]
+        lib.spmm_batch_destroy.argtypes = [vp]
+        lib.spmm_batch_workspace_size.argtypes = [vp, P(sz)]
+        lib.spmm_batch_set_shapes.argtypes = [vp, P(i32), P(i32), P(i32), vp]
+        lib.spmm_batch_get_shapes.argtypes = [vp, P(i32), P(i32), P(i32)]
+        lib.spmm_csr_batched.argtypes = [vp, vp, sz, vp]
+        lib.spmm_batch_graph_launch.argtypes = [vp, vp, sz, vp]
+        lib.spmm_batch_autotune.argtypes = [vp, vp, sz, i32, vp, P(ctypes.c_float)]
         lib.spmm_csr_noalloc.argtypes = [vp, vp, vp, i32, vp, vp, i32, vp, i64, vp, i64, i64, i64,
                                          i64, i64, i32, i32, f32, vp]
         for name in EXPORTED:
@@ -269,3 +290,83 @@ def spmm_quantize_rows(X, dtype: int, Xq, scale=None, stream=None) -> None:
     _check(load_library().spmm_quantize_rows(_ptr(X), rows, cols, int(X.stride(0)), int(dtype),
                                              _ptr(Xq), int(Xq.stride(0)), _ptr(scale),
                                              _stream(stream)), "spmm_quantize_rows")
+
+
+class Batch:
+    """Owner of a spmm_batch handle: many products in one persistent launch.
+
+    ``problems`` is a list of dicts with keys rowptr, colind, vals, B, C (device
+    tensors), M, K, N and optionally a_scale, b_scale, beta, tile_rows,
+    tile_cols, chunk_items.  The tensors must outlive the batch."""
+
+    def __init__(self, problems, stream=None):
+        lib = load_library()
+        self.count = len(problems)
+        self._keep = problems
+        arr = (spmm_problem * self.count)()
+        a_dt = b_dt = None
+        for k, q in enumerate(problems):
+            e = arr[k]
+            e.rowptr, e.colind = q["rowptr"].data_ptr(), q["colind"].data_ptr()
+            e.vals = q["vals"].data_ptr()
+            e.a_scale = q["a_scale"].data_ptr() if q.get("a_scale") is not None else None
+            e.B, e.C = q["B"].data_ptr(), q["C"].data_ptr()
+            e.b_scale = q["b_scale"].data_ptr() if q.get("b_scale") is not None else None
+            e.M, e.K, e.N = int(q["M"]), int(q["K"]), int(q["N"])
+            e.nnz = int(q["colind"].numel())
+            e.ldb, e.ldc = int(q["B"].stride(0)), int(q["C"].stride(0))
+            e.beta = float(q.get("beta", 0.0))
+            e.tile_rows = int(q.get("tile_rows", 0))
+            e.tile_cols = int(q.get("tile_cols", 0))
+            e.chunk_items = int(q.get("chunk_items", 0))
+            a_dt = dtype_code(q["vals"].dtype) if a_dt is None else a_dt
+            b_dt = dtype_code(q["B"].dtype) if b_dt is None else b_dt
+        self.handle = ctypes.c_void_p()
+        _check(lib.spmm_batch_create(ctypes.byref(self.handle), arr, self.count, a_dt, b_dt,
+                                     _stream(stream)), "spmm_batch_create")
+        n = ctypes.c_size_t()
+        _check(lib.spmm_batch_workspace_size(self.handle, ctypes.byref(n)),
+               "spmm_batch_workspace_size")
+        self.workspace_bytes = int(n.value)
+
+    def run(self, ws, stream=None):
+        _check(load_library().spmm_csr_batched(self.handle, _ptr(ws), ws.numel(),
+                                               _stream(stream)), "spmm_csr_batched")
+
+    def graph_launch(self, ws, stream=None):
+        _check(load_library().spmm_batch_graph_launch(self.handle, _ptr(ws), ws.numel(),
+                                                      _stream(stream)), "spmm_batch_graph_launch")
+
+    def autotune(self, ws, reps=3, stream=None) -> float:
+        ms = ctypes.c_float()
+        _check(load_library().spmm_batch_autotune(self.handle, _ptr(ws), ws.numel(), int(reps),
+                                                  _stream(stream), ctypes.byref(ms)),
+               "spmm_batch_autotune")
+        return float(ms.value)
+
+    def shapes(self):
+        n = self.count
+        tr, tc, d = (ctypes.c_int32 * n)(), (ctypes.c_int32 * n)(), (ctypes.c_int32 * n)()
+        _check(load_library().spmm_batch_get_shapes(self.handle, tr, tc, d),
+               "spmm_batch_get_shapes")
+        return list(tr), list(tc), list(d)
+
+    def set_shapes(self, tile_rows=None, tile_cols=None, chunk_items=None, stream=None):
+        n = self.count
+
+        def arr(v):
+            return None if v is None else (ctypes.c_int32 * n)(*[int(x) for x in v])
+        _check(load_library().spmm_batch_set_shapes(self.handle, arr(tile_rows), arr(tile_cols),
+                                                    arr(chunk_items), _stream(stream)),
+               "spmm_batch_set_shapes")
+
+    def close(self):
+        if self.handle:
+            load_library().spmm_batch_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

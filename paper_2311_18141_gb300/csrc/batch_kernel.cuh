@@ -1,0 +1,105 @@
+// Batched persistent SpMM: many independent products C_p = beta_p*C_p + A_p*B_p
+// in one launch.
+//
+// Every problem keeps its own merge-path plan.  Its work units (chunk, column
+// block) are numbered after those of the problems before it (item_base), and
+// the warps of one persistent grid reserve items from a single global counter
+// with atomicAdd (Algorithm 3's fetch-and-add, over the whole batch): a warp
+// that finishes a small problem moves straight on to the next item of any
+// problem.  The host orders problems by decreasing work, so the largest are
+// reserved first.  Each warp copies the descriptor of the problem it is working
+// on into its own slot of shared memory, then runs the same unit code as the
+// single-problem kernel, with the problem's lane-group shape chosen at run time
+// from five compiled shapes.
+#pragma once
+
+#include "spmm_kernel.cuh"
+
+#ifndef SPMM_BATCH_MINBLOCKS
+#define SPMM_BATCH_MINBLOCKS 2   // five inlined shapes need a larger register budget
+#endif
+
+namespace spmm {
+
+// One problem of a batch as the device sees it.  Scratch pointers inside `p`
+// are filled in per call from the workspace base and the offsets below.
+struct BatchEntry {
+    Problem p;
+    int64_t piece_off;   // byte offset of this problem's piece counters in the workspace
+    int64_t slot_off;    // byte offset of its partial-row slots
+    int32_t lpn;         // lanes per nonzero of its column blocks (2, 4, 8, 16 or 32)
+    int32_t pad;
+};
+
+static_assert(sizeof(BatchEntry) % 4 == 0, "descriptor copied as 32-bit words");
+
+constexpr int kBatchWarps = 8;
+
+template <class TA, class TB, int LPN>
+__device__ __forceinline__ void batch_unit(const Problem& p, int i, int j, int c, int lane) {
+    using K = KCfg<TA, TB, LPN, 1>;
+    const LaneCols<K::VPL> lc = lane_cols<K, K::VPL, K::LPN>(p, j, lane % K::LPN);
+    const LaneCols<K::VPS> ls = lane_cols<K, K::VPS, K::SUB>(p, j, lane % K::SUB);
+    process_unit<K>(p, i, j, c, lc, ls, lane);
+}
+
+template <class TA, class TB>
+__global__ void __launch_bounds__(kBatchWarps * 32, SPMM_BATCH_MINBLOCKS)
+spmm_csr_batched_kernel(const BatchEntry* __restrict__ table,
+                        const int64_t* __restrict__ item_base, int count, char* ws,
+                        int* counter) {
+    __shared__ Problem sp[kBatchWarps];
+    const int lane = threadIdx.x & 31;
+    const int w = threadIdx.x >> 5;
+    const int64_t total = item_base[count];
+    int cur = -1;   // problem whose descriptor is in sp[w]
+    while (true) {
+        int item = 0;
+        if (lane == 0) item = atomicAdd(counter, 1);
+        item = __shfl_sync(kFull, item, 0);
+        if ((int64_t)item >= total) break;
+        // problem owning the item: largest q with item_base[q] <= item
+        int lo = 0, hi = count - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (item_base[mid] <= (int64_t)item) lo = mid;
+            else hi = mid - 1;
+        }
+        const BatchEntry* e = table + lo;
+        if (lo != cur) {
+            __syncwarp();
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(&e->p);
+            uint32_t* dst = reinterpret_cast<uint32_t*>(&sp[w]);
+            for (int k = lane; k < (int)(sizeof(Problem) / 4); k += 32) dst[k] = src[k];
+            __syncwarp();
+            if (lane == 0) {
+                sp[w].status = reinterpret_cast<int32_t*>(ws);
+                sp[w].piece_cnt = reinterpret_cast<int32_t*>(ws + e->piece_off);
+                sp[w].slots = reinterpret_cast<float*>(ws + e->slot_off);
+            }
+            __syncwarp();
+            cur = lo;
+        }
+        const Problem& p = sp[w];
+        const int local = item - (int)item_base[lo];
+        const int gcl = local / p.TC;
+        const int j = local - gcl * p.TC;
+        // row block of the chunk: largest i with blk_base[i] <= gcl
+        int il = 0, ih = p.TR - 1;
+        while (il < ih) {
+            const int mid = (il + ih + 1) >> 1;
+            if (p.blk_base[mid] <= gcl) il = mid;
+            else ih = mid - 1;
+        }
+        const int c = gcl - p.blk_base[il];
+        switch (e->lpn) {
+            case 2: batch_unit<TA, TB, 2>(p, il, j, c, lane); break;
+            case 4: batch_unit<TA, TB, 4>(p, il, j, c, lane); break;
+            case 8: batch_unit<TA, TB, 8>(p, il, j, c, lane); break;
+            case 16: batch_unit<TA, TB, 16>(p, il, j, c, lane); break;
+            default: batch_unit<TA, TB, 32>(p, il, j, c, lane); break;
+        }
+    }
+}
+
+}  // namespace spmm

@@ -70,7 +70,7 @@ __device__ __forceinline__ void st_cg_f4(float* p, float4 v) {
 
 // c += a * b on two FP32 lanes at once (packed FFMA2 on sm_100 and later).
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
-#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000)
+#if defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000) && !defined(SPMM_SCALAR_FMA)
     return __ffma2_rn(a, b, c);
 #else
     return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));

@@ -1,6 +1,7 @@
 // Instantiates the persistent SpMM kernel for one (A value type, B type).
 #pragma once
 
+#include "batch_kernel.cuh"
 #include "launch.cuh"
 #include "spmm_kernel.cuh"
 
@@ -37,6 +38,24 @@ cudaError_t launch_pair(int lpn, int vpl, const Problem& p, const LaunchOpts& o,
     }
 }
 
+template <class TA, class TB>
+cudaError_t launch_batched(const BatchEntry* table, const int64_t* item_base, int count, char* ws,
+                           int* counter, int64_t max_items, int ctas_per_sm, cudaStream_t s) {
+    auto kern = spmm_csr_batched_kernel<TA, TB>;
+    const int threads = kBatchWarps * 32;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
+    int64_t grid = (int64_t)device_sm_count() * per_sm;
+    const int64_t need = (max_items + kBatchWarps - 1) / kBatchWarps;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, threads, 0, s>>>(table, item_base, count, ws, counter);
+    return cudaGetLastError();
+}
+
 }  // namespace spmm
 
 #define SPMM_DEFINE_LAUNCHER(a, b, TA, TB)                                               \
@@ -44,5 +63,10 @@ cudaError_t launch_pair(int lpn, int vpl, const Problem& p, const LaunchOpts& o,
     cudaError_t launch_spmm_##a##_##b(int lpn, int vpl, const Problem& p,                \
                                       const LaunchOpts& o, cudaStream_t s) {              \
         return launch_pair<TA, TB>(lpn, vpl, p, o, s);                                    \
+    }                                                                                     \
+    cudaError_t launch_batched_##a##_##b(const BatchEntry* t, const int64_t* ib, int n,  \
+                                         char* ws, int* ctr, int64_t mx, int cps,         \
+                                         cudaStream_t s) {                                \
+        return launch_batched<TA, TB>(t, ib, n, ws, ctr, mx, cps, s);                     \
     }                                                                                     \
     }

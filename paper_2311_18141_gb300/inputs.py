@@ -168,6 +168,23 @@ def _distinct_sorted_columns(row_of: torch.Tensor, K: int, seed: int, device) ->
     non-decreasing), redrawing collisions until every row's columns are distinct.
     Returns int64 keys row*K + col, sorted."""
     n = row_of.numel()
+    if n == 0:
+        return row_of.clone()
+    lens = torch.bincount(row_of)
+    dense = (lens * 8 >= K).nonzero().flatten()
+    if dense.numel() > 0:
+        # rows asking for at least K/8 columns: rank every column of the row by a
+        # hashed key and keep the first L (redraws would converge too slowly)
+        keep = ~torch.isin(row_of, dense)
+        sparse_keys = _distinct_sorted_columns(row_of[keep], K, seed, device)
+        cand = torch.arange(K, dtype=torch.int64, device=device)
+        parts = [sparse_keys]
+        for r in dense.tolist():
+            L = int(lens[r])
+            score = hash_u32(r * (K + 1) + cand, seed, STREAM_COLS + 100)
+            pick = torch.sort(torch.argsort(score)[:L]).values
+            parts.append(r * K + pick)
+        return torch.sort(torch.cat(parts)).values
     slot = torch.arange(n, dtype=torch.int64, device=device)
     cols = hash_u32(slot * 64, seed, STREAM_COLS) % K
     for attempt in range(1, 64):
