@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="rmat", choices=["rmat", "precision", "gcn", "batch"],
+                    help="rmat: the benchmark line; the others report the precision, "
+                         "backward and batched forms")
     return ap.parse_args()
 
 
@@ -369,8 +372,186 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def _time_ms(fn, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def run_precision(args):
+    """FP16 A values; B of width 256 stored FP32, BF16 and E4M3 + per-row scales;
+    FP32 accumulation.  Time per storage format and error against the FP64
+    oracle on a sample of rows (max and RMS of |C - C64| / (|A||B|))."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_2311_18141_gb300 import binding
+    dev = torch.device("cuda")
+    binding.load_library()
+    N = 256
+    A, B = make_workload(args.scale, N, dev)
+    v16 = A.vals.to(torch.float16)
+    M, K, nnz = A.M, A.K, A.nnz
+    TR, TC = (int(x) for x in args.grid.split("x"))
+    stream = torch.cuda.current_stream()
+    rows = torch.arange(0, M, 97, device=dev)
+    rows_h = rows.cpu().numpy()
+    rp, ci = A.rowptr.cpu().numpy(), A.colind.cpu().numpy()
+    v64 = v16.float().cpu().numpy().astype(np.float64)
+    Bh = B.cpu().numpy()
+    ref = oracle.spmm_rows(rp, ci, v64, Bh, rows_h)
+    bound = oracle.spmm_rows(rp, ci, np.abs(v64), np.abs(Bh.astype(np.float64)), rows_h)
+    out = {}
+    for fmt in ("f32", "bf16", "e4m3"):
+        scale = None
+        if fmt == "f32":
+            Bq = B
+        elif fmt == "bf16":
+            Bq = torch.empty(K, N, dtype=torch.bfloat16, device=dev)
+            binding.spmm_quantize_rows(B, binding.SPMM_BF16, Bq)
+        else:
+            Bq = torch.empty(K, N, dtype=torch.uint8, device=dev)
+            scale = torch.empty(K, dtype=torch.float32, device=dev)
+            binding.spmm_quantize_rows(B, binding.SPMM_E4M3, Bq, scale)
+        C = torch.empty(M, N, device=dev)
+        plan = binding.Plan(A.rowptr, M, K, nnz, N, TR, TC)
+        ws = binding.workspace(plan.workspace_bytes, dev)
+
+        def step():
+            binding.spmm_csr(A.rowptr, A.colind, v16, Bq, C, M, K, N, nnz, b_scale=scale,
+                             plan=plan, ws=ws, stream=stream)
+        ms = _time_ms(step, args.steps, args.warmup, stream)
+        w_b = {"f32": 4, "bf16": 2, "e4m3": 1}[fmt]
+        algo = min_bytes(M, K, N, nnz, w_val=2, w_b=w_b) + (4 * K if fmt == "e4m3" else 0)
+        got = C[rows].double().cpu().numpy()
+        rel = np.abs(got - ref) / np.maximum(bound, 1e-30)
+        out[fmt] = {"ms": ms, "gflops": 2.0 * nnz * N / ms / 1e6,
+                    "hbm_frac": algo / (ms * 1e-3) / 1e9 / measured_peaks()[0],
+                    "err_max": float(rel.max()), "err_rms": float(np.sqrt((rel ** 2).mean()))}
+        plan.close()
+    print(json.dumps({"workload": f"rmat-s{args.scale}-fp16A-n256", "tile_grid": args.grid,
+                      "nnz": nnz, "results": out, "error_sample_rows": int(rows.numel())}),
+          flush=True)
+
+
+def run_gcn(args):
+    """GCN layer C = A_hat (X W) on the symmetrised R-MAT scale-18 graph: forward
+    SpMM, the device transpose, dB = A_hat^T dC and SDDMM, timed separately."""
+    import torch
+    from paper_2311_18141_gb300 import binding, inputs
+    from paper_2311_18141_gb300.autograd import SparseCSR
+    dev = torch.device("cuda")
+    binding.load_library()
+    torch.backends.cuda.matmul.allow_tf32 = False
+    A = inputs.gcn_normalized_adjacency(18, 16, seed=4, device=dev)
+    X = inputs.dense_normal(A.M, 128, seed=55, device=dev)
+    W = inputs.glorot_uniform(128, 64, seed=56, device=dev)
+    B = X @ W
+    dC = inputs.dense_normal(A.M, 64, seed=57, device=dev)
+    N, M, K, nnz = 64, A.M, A.K, A.nnz
+    S = SparseCSR(A.rowptr, A.colind, M, K, tile_rows=8)
+    stream = torch.cuda.current_stream()
+    C = torch.empty(M, N, device=dev)
+    plan, ws = S.plan(N)
+    fwd = _time_ms(lambda: binding.spmm_csr(A.rowptr, A.colind, A.vals, B, C, M, K, N, nnz,
+                                            plan=plan, ws=ws, stream=stream),
+                   args.steps, args.warmup, stream)
+    colptr = torch.empty(K + 1, dtype=torch.int32, device=dev)
+    rowind = torch.empty(nnz, dtype=torch.int32, device=dev)
+    tv = torch.empty(nnz, device=dev)
+    perm = torch.empty(nnz, dtype=torch.int32, device=dev)
+    tws = binding.workspace(binding.spmm_csr_transpose_workspace_size(M, K, nnz), dev)
+    tr = _time_ms(lambda: binding.spmm_csr_transpose(A.rowptr, A.colind, A.vals, M, K, nnz, colptr,
+                                                     rowind, tv, perm, tws, stream=stream),
+                  args.steps, args.warmup, stream)
+    tplan, tws2 = S.plan(N, transpose=True)
+    dB = torch.empty(K, N, device=dev)
+    bwd_b = _time_ms(lambda: binding.spmm_csr(colptr, rowind, tv, dC, dB, K, M, N, nnz,
+                                              plan=tplan, ws=tws2, stream=stream),
+                     args.steps, args.warmup, stream)
+    splan, sws = S.plan(N, sddmm=True)
+    dv = torch.empty(nnz, device=dev)
+    sd = _time_ms(lambda: binding.spmm_sddmm_csr(A.rowptr, A.colind, dC, B, dv, M, K, N, nnz,
+                                                 plan=splan, ws=sws, stream=stream),
+                  args.steps, args.warmup, stream)
+    fwd_bytes = min_bytes(M, K, N, nnz)
+    sd_bytes = 4 * (M + 1) + 4 * nnz + 4 * M * N + 4 * K * N + 4 * nnz
+    peak = measured_peaks()[0]
+    print(json.dumps({"workload": "gcn-rmat-s18-n64", "nnz": nnz,
+                      "forward_ms": fwd, "forward_hbm_frac": fwd_bytes / (fwd * 1e-3) / 1e9 / peak,
+                      "transpose_ms": tr, "dB_ms": bwd_b,
+                      "sddmm_ms": sd, "sddmm_hbm_frac": sd_bytes / (sd * 1e-3) / 1e9 / peak}),
+          flush=True)
+
+
+def run_batch(args):
+    """512 uneven BF16 products (rows log-uniform 1e3..2e5, Poisson nnz/row with
+    mean U[8,64], N in {16, 64, 128}): one graph-replayed persistent launch,
+    before and after autotuning, against 512 sequential spmm_csr launches."""
+    import torch
+    from paper_2311_18141_gb300 import binding, inputs
+    dev = torch.device("cuda")
+    binding.load_library()
+    specs = inputs.batch_specs(512, seed=5)
+    probs, flops, algo = [], 0.0, 0
+    for sp in specs:
+        A = inputs.poisson_csr(sp.rows, sp.rows, sp.mean_nnz, seed=sp.seed, device=dev)
+        B = inputs.dense_normal(A.K, sp.N, seed=sp.seed + 1, device=dev).to(torch.bfloat16)
+        C = torch.empty(A.M, sp.N, device=dev)
+        probs.append(dict(rowptr=A.rowptr, colind=A.colind, vals=A.vals.to(torch.bfloat16),
+                          B=B, C=C, M=A.M, K=A.K, N=sp.N))
+        flops += 2.0 * A.nnz * sp.N
+        algo += min_bytes(A.M, A.K, sp.N, A.nnz, w_val=2, w_b=2)
+    stream = torch.cuda.current_stream()
+    # sequential: one plan and one spmm_csr launch per product
+    seq = []
+    for q in probs:
+        pl = binding.Plan(q["rowptr"], q["M"], q["K"], q["colind"].numel(), q["N"], 1, 1)
+        seq.append((q, pl, binding.workspace(pl.workspace_bytes, dev)))
+
+    def run_seq():
+        for q, pl, w in seq:
+            binding.spmm_csr(q["rowptr"], q["colind"], q["vals"], q["B"], q["C"], q["M"], q["K"],
+                             q["N"], q["colind"].numel(), plan=pl, ws=w, stream=stream)
+    seq_ms = _time_ms(run_seq, max(3, args.steps // 10), 2, stream)
+    batch = binding.Batch(probs)
+    bws = binding.workspace(batch.workspace_bytes, dev)
+    graph_ms = _time_ms(lambda: batch.graph_launch(bws, stream), args.steps, args.warmup, stream)
+    tune_ms = batch.autotune(bws, reps=3)
+    tuned_ms = _time_ms(lambda: batch.graph_launch(bws, stream), args.steps, args.warmup, stream)
+    peak = measured_peaks()[0]
+    nnz = sum(q["colind"].numel() for q in probs)
+    print(json.dumps({"workload": "batch-512-bf16", "nnz": nnz, "gflop": flops / 1e9,
+                      "algorithmic_bytes": algo, "sequential_ms": seq_ms,
+                      "graph_ms": graph_ms, "autotuned_graph_ms": tuned_ms,
+                      "autotune_best_ms": tune_ms,
+                      "speedup_vs_sequential": seq_ms / tuned_ms,
+                      "tuned_gflops": flops / (tuned_ms * 1e-3) / 1e9,
+                      "tuned_hbm_frac": algo / (tuned_ms * 1e-3) / 1e9 / peak}), flush=True)
+    for _, pl, _ in seq:
+        pl.close()
+    batch.close()
+
+
 def main():
     args = parse()
+    if args.workload == "precision":
+        run_precision(args)
+        return
+    if args.workload == "gcn":
+        run_gcn(args)
+        return
+    if args.workload == "batch":
+        run_batch(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -20,9 +20,10 @@
 // Inside a unit a warp loads the row pointers of 32 rows at once.  Rows with
 // at most SHORT_MAX nonzeros (empty rows included) are processed SUB lanes
 // per row, all such rows of the batch in parallel, each lane gathering VPS
-// 16-byte vectors of B per nonzero, one nonzero at a time.  Longer rows and split rows are walked by
-// the whole warp: LPN-lane groups interleaved over the nonzeros, U gathers in
-// flight per lane, then a shuffle reduction across the groups.
+// 16-byte vectors of B per nonzero, one nonzero at a time.  Longer rows and
+// split rows are walked by the whole warp: each LPN-lane group takes its own
+// run of nonzeros of every 32-nonzero batch, UB gathers in flight per lane,
+// then a shuffle reduction across the groups.
 #pragma once
 
 #include "common.cuh"
@@ -53,7 +54,7 @@ struct KCfg {
     // gathers in flight per lane on the whole-warp path: up to SPMM_LONG_UNROLL
     // steps of VPL vectors, never more steps than a 32-nonzero batch has
     static constexpr int UB0 = SPMM_LONG_UNROLL / VPL < 1 ? 1 : SPMM_LONG_UNROLL / VPL;
-    static constexpr int UB = (32 / G) < UB0 ? (32 / G) : UB0;
+    static constexpr int UB = LPN < UB0 ? LPN : UB0;           // steps per batch = LPN
     // Short rows: SUB lanes per row, each lane VPS vectors (about 16 floats),
     // RPP rows of a 32-row batch per pass, SUB passes per batch.
     static constexpr int WF = LPN * VPL * EPV;                 // floats of a column block
@@ -202,11 +203,14 @@ __device__ __forceinline__ void piece_row(const Problem& p, int i, int j, int gc
     store_vecs<K, K::VPL, K::LPN>(p, r, sum, lc);
 }
 
-// Whole-warp walk of nonzeros [rs, rs+L) of one row: group g takes nonzeros
-// g, g+G, g+2G, ...; returns the group-summed vector in every group.  The
-// column indices and values of the next 32 nonzeros are fetched while the
-// current 32 are gathered (Algorithm 2's prefetch of the next tile, at warp
-// scale); UB gathers per lane are in flight before their FMAs.
+// Whole-warp walk of nonzeros [rs, rs+L) of one row.  The row is taken 32
+// nonzeros at a time, lane l holding nonzero l of the batch; group g owns the
+// contiguous nonzeros g*LPN .. g*LPN+LPN-1 of each batch, so step s of every
+// group reads lane s of its own LPN-lane segment (an immediate shuffle index).
+// The next batch's column indices and values are fetched while the current
+// one is gathered (Algorithm 2's prefetch of the next tile, at warp scale), and
+// UB gathers per lane are in flight before their FMAs.  Returns the vector
+// summed over the groups in every group.
 template <class K>
 __device__ __forceinline__ void row_warp(const Problem& p, int rs, int L,
                                          const LaneCols<K::VPL>& lc, float2* acc, int lane) {
@@ -234,29 +238,54 @@ __device__ __forceinline__ void row_warp(const Problem& p, int rs, int L,
                 val_n = aval<typename K::TA, true>(p.vals, (int64_t)rs + idx);
             }
         }
-        const int nsteps = (cnt + K::G - 1) / K::G;
-#pragma unroll 1
-        for (int t0 = 0; t0 < nsteps; t0 += K::UB) {
-            uint4 bv[K::UB][K::VPL];
-            float av[K::UB];
+        if (cnt == 32) {
+            // full batch: every step of every group is a nonzero
 #pragma unroll
-            for (int u = 0; u < K::UB; ++u) {
-                const int src = (t0 + u) * K::G + g;
-                const int cc = __shfl_sync(kFull, col, src & 31);
-                av[u] = __shfl_sync(kFull, v, src & 31);
-                const char* rp = brow(lc, cc);
-                if (src < cnt) {
+            for (int s0 = 0; s0 < K::LPN; s0 += K::UB) {
+                uint4 bv[K::UB][K::VPL];
+                float av[K::UB];
+#pragma unroll
+                for (int u = 0; u < K::UB; ++u) {
+                    const int cc = __shfl_sync(kFull, col, s0 + u, K::LPN);
+                    av[u] = __shfl_sync(kFull, v, s0 + u, K::LPN);
+                    const char* rp = brow(lc, cc);
 #pragma unroll
                     for (int q = 0; q < K::VPL; ++q) bv[u][q] = ld_b16(rp + lc.qoff[q]);
                 }
-            }
 #pragma unroll
-            for (int u = 0; u < K::UB; ++u) {
-                if ((t0 + u) * K::G + g < cnt) {
+                for (int u = 0; u < K::UB; ++u) {
                     const float2 a2 = make_float2(av[u], av[u]);
 #pragma unroll
                     for (int q = 0; q < K::VPL; ++q)
                         fma_vec<typename K::TB>(acc + q * (K::EPV / 2), a2, bv[u][q]);
+                }
+            }
+        } else {
+            // last, partial batch: group g has cg nonzeros
+            const int cg = min(max(cnt - g * K::LPN, 0), K::LPN);
+            const int steps = min(cnt, K::LPN);
+#pragma unroll 1
+            for (int s0 = 0; s0 < steps; s0 += K::UB) {
+                uint4 bv[K::UB][K::VPL];
+                float av[K::UB];
+#pragma unroll
+                for (int u = 0; u < K::UB; ++u) {
+                    const int cc = __shfl_sync(kFull, col, (s0 + u) & (K::LPN - 1), K::LPN);
+                    av[u] = __shfl_sync(kFull, v, (s0 + u) & (K::LPN - 1), K::LPN);
+                    const char* rp = brow(lc, cc);
+                    if (s0 + u < cg) {
+#pragma unroll
+                        for (int q = 0; q < K::VPL; ++q) bv[u][q] = ld_b16(rp + lc.qoff[q]);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < K::UB; ++u) {
+                    if (s0 + u < cg) {
+                        const float2 a2 = make_float2(av[u], av[u]);
+#pragma unroll
+                        for (int q = 0; q < K::VPL; ++q)
+                            fma_vec<typename K::TB>(acc + q * (K::EPV / 2), a2, bv[u][q]);
+                    }
                 }
             }
         }
