@@ -35,12 +35,21 @@ static_assert(sizeof(BatchEntry) % 4 == 0, "descriptor copied as 32-bit words");
 
 constexpr int kBatchWarps = 8;
 
+// Staging bytes per warp: the largest of the five shapes.
+template <class TA, class TB>
+__host__ __device__ constexpr int batch_stage_bytes() {
+    constexpr int a = KCfg<TA, TB, 2, 1>::STAGE_BYTES, b = KCfg<TA, TB, 4, 1>::STAGE_BYTES;
+    constexpr int c = KCfg<TA, TB, 8, 1>::STAGE_BYTES;
+    return a > b ? (a > c ? a : c) : (b > c ? b : c);
+}
+
 template <class TA, class TB, int LPN>
-__device__ __forceinline__ void batch_unit(const Problem& p, int i, int j, int c, int lane) {
+__device__ __forceinline__ void batch_unit(const Problem& p, int i, int j, int c, int lane,
+                                           uint32_t sbase) {
     using K = KCfg<TA, TB, LPN, 1>;
     const LaneCols<K::VPL> lc = lane_cols<K, K::VPL, K::LPN>(p, j, lane % K::LPN);
     const LaneCols<K::VPS> ls = lane_cols<K, K::VPS, K::SUB>(p, j, lane % K::SUB);
-    process_unit<K>(p, i, j, c, lc, ls, lane);
+    process_unit<K>(p, i, j, c, lc, ls, lane, sbase);
 }
 
 template <class TA, class TB>
@@ -51,6 +60,8 @@ spmm_csr_batched_kernel(const BatchEntry* __restrict__ table,
     __shared__ Problem sp[kBatchWarps];
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(spmm_dyn_smem) +
+                           (uint32_t)(w * batch_stage_bytes<TA, TB>() + lane * 16);
     const int64_t total = item_base[count];
     int cur = -1;   // problem whose descriptor is in sp[w]
     while (true) {
@@ -93,11 +104,11 @@ spmm_csr_batched_kernel(const BatchEntry* __restrict__ table,
         }
         const int c = gcl - p.blk_base[il];
         switch (e->lpn) {
-            case 2: batch_unit<TA, TB, 2>(p, il, j, c, lane); break;
-            case 4: batch_unit<TA, TB, 4>(p, il, j, c, lane); break;
-            case 8: batch_unit<TA, TB, 8>(p, il, j, c, lane); break;
-            case 16: batch_unit<TA, TB, 16>(p, il, j, c, lane); break;
-            default: batch_unit<TA, TB, 32>(p, il, j, c, lane); break;
+            case 2: batch_unit<TA, TB, 2>(p, il, j, c, lane, sbase); break;
+            case 4: batch_unit<TA, TB, 4>(p, il, j, c, lane, sbase); break;
+            case 8: batch_unit<TA, TB, 8>(p, il, j, c, lane, sbase); break;
+            case 16: batch_unit<TA, TB, 16>(p, il, j, c, lane, sbase); break;
+            default: batch_unit<TA, TB, 32>(p, il, j, c, lane, sbase); break;
         }
     }
 }

@@ -38,6 +38,26 @@ __device__ __forceinline__ uint4 ld_b16(const void* p) {
     return __ldg(reinterpret_cast<const uint4*>(p));
 }
 
+// 16-byte asynchronous copy global -> shared (L1-allocating); copies
+// `src_bytes` (16 or 0) and zero-fills the rest of the 16 bytes.
+__device__ __forceinline__ void cp_async16(uint32_t smem_addr, const void* gptr, int src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;"
+                 :: "r"(smem_addr), "l"(gptr), "r"(src_bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory");
+}
+__device__ __forceinline__ uint4 lds128(uint32_t smem_addr) {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(smem_addr));
+    return v;
+}
+
 // Relaxed GPU-scope read of a work counter.
 __device__ __forceinline__ int32_t ld_relaxed(const int32_t* p) {
     int32_t v;

@@ -34,6 +34,9 @@
 #ifndef SPMM_LONG_UNROLL
 #define SPMM_LONG_UNROLL 4 // B gathers in flight per lane on the whole-warp path
 #endif
+#ifndef SPMM_STAGE
+#define SPMM_STAGE 1       // stage whole-warp gathers through shared memory (groups <= 8 lanes)
+#endif
 
 namespace spmm {
 
@@ -63,7 +66,15 @@ struct KCfg {
     static constexpr int RPP = 32 / SUB;
     static constexpr int NS = VPS * EPV;                       // short-path floats per lane
     static constexpr int SHORT_MAX = 16;                       // longer rows: whole warp
+    // Whole-warp gathers staged through shared memory with cp.async, two
+    // 32-nonzero batches in flight per warp (each lane LPN 16-byte slots per
+    // batch); used when a group is at most 8 lanes wide and one vector deep.
+    static constexpr bool STAGED = SPMM_STAGE && LPN <= 8 && VPL == 1;
+    static constexpr int STAGE_BYTES = STAGED ? 2 * LPN * 32 * 16 : 0;   // per warp
 };
+
+// Dynamic shared memory of the persistent kernels (staging buffers).
+extern __shared__ uint4 spmm_dyn_smem[];
 
 // Per-lane view of a column block: where this lane's vectors start in a B
 // row and a C row, and which of them fall inside the block.  Vectors outside
@@ -299,6 +310,82 @@ __device__ __forceinline__ void row_warp(const Problem& p, int rs, int L,
         }
 }
 
+// The whole-warp walk with shared-memory staging.  Batch b's gathers are
+// issued as 16-byte cp.async copies into stage b&1 while batch b-1 is summed
+// from the other stage.  Lane l issues and later reads its own slots only, so
+// cp.async.wait_group alone orders the copy before the read.  Slots of padding
+// lanes are zero-filled and their values are 0, so no step needs a predicate.
+// `sbase` is this lane's first slot: warp region + lane * 16 bytes.
+template <class K>
+__device__ __forceinline__ void row_warp_staged(const Problem& p, int rs, int L,
+                                                const LaneCols<1>& lc, float2* acc, int lane,
+                                                uint32_t sbase) {
+    const int g = lane / K::LPN;
+#pragma unroll
+    for (int e = 0; e < K::NE / 2; ++e) acc[e] = make_float2(0.0f, 0.0f);
+    const int nb = (L + 31) >> 5;
+    // registers of the batch being issued (col_i, val_i) and of the one after
+    int col_i = 0, col_n = 0;
+    float val_i = 0.0f, val_n = 0.0f;
+    if (lane < L) {
+        col_i = ld_stream_i32(p.colind + rs + lane);
+        val_i = aval<typename K::TA, true>(p.vals, (int64_t)rs + lane);
+        if (p.b_scale) val_i *= __ldg(p.b_scale + col_i);
+    }
+    if (32 + lane < L) {
+        col_n = ld_stream_i32(p.colind + rs + 32 + lane);
+        val_n = aval<typename K::TA, true>(p.vals, (int64_t)rs + 32 + lane);
+    }
+    auto issue = [&](int b, int col) {
+        const int cnt = min(32, L - 32 * b);
+        const uint32_t st = sbase + (uint32_t)((b & 1) * K::LPN * 32 * 16);
+#pragma unroll
+        for (int s = 0; s < K::LPN; ++s) {
+            const int cc = __shfl_sync(kFull, col, s, K::LPN);
+            const int ok = (g * K::LPN + s < cnt) ? 16 : 0;
+            cp_async16(st + (uint32_t)(s * 32 * 16), brow(lc, cc), ok);
+        }
+        cp_async_commit();
+    };
+    issue(0, col_i);
+    float val_c = val_i;   // values of the batch being summed
+#pragma unroll 1
+    for (int b = 0; b < nb; ++b) {
+        if (b + 1 < nb) {
+            if (p.b_scale && 32 * (b + 1) + lane < L) val_n *= __ldg(p.b_scale + col_n);
+            issue(b + 1, col_n);
+            const float val_next = val_n;
+            col_i = col_n;
+            val_i = val_next;
+            col_n = 0;
+            val_n = 0.0f;
+            const int idx = 32 * (b + 2) + lane;
+            if (idx < L) {
+                col_n = ld_stream_i32(p.colind + rs + idx);
+                val_n = aval<typename K::TA, true>(p.vals, (int64_t)rs + idx);
+            }
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        const uint32_t st = sbase + (uint32_t)((b & 1) * K::LPN * 32 * 16);
+#pragma unroll
+        for (int s = 0; s < K::LPN; ++s) {
+            const float a = __shfl_sync(kFull, val_c, s, K::LPN);
+            const uint4 bv = lds128(st + (uint32_t)(s * 32 * 16));
+            fma_vec<typename K::TB>(acc, make_float2(a, a), bv);
+        }
+        val_c = val_i;
+    }
+#pragma unroll
+    for (int off = K::LPN; off < 32; off <<= 1)
+#pragma unroll
+        for (int e = 0; e < K::NE / 2; ++e) {
+            acc[e].x += __shfl_xor_sync(kFull, acc[e].x, off);
+            acc[e].y += __shfl_xor_sync(kFull, acc[e].y, off);
+        }
+}
+
 // Short rows of the batch: SUB lanes per row, RPP rows per pass.  Each lane
 // fetches the next nonzero's column and value while gathering the current one.
 template <class K>
@@ -354,7 +441,8 @@ __device__ __forceinline__ void short_rows(const Problem& p, int rb, unsigned sm
 template <class K>
 __device__ __forceinline__ void process_unit(const Problem& p, int i, int j, int c,
                                              const LaneCols<K::VPL>& lc,
-                                             const LaneCols<K::VPS>& ls, int lane) {
+                                             const LaneCols<K::VPS>& ls, int lane,
+                                             uint32_t sbase) {
     const int g = lane / K::LPN;
     const int gc = p.blk_base[i] + c;
     const int bi = gc + i;
@@ -403,7 +491,8 @@ __device__ __forceinline__ void process_unit(const Problem& p, int i, int j, int
             const unsigned flags =
                 __shfl_sync(kFull, (piece ? 1u : 0u) | (tail ? 2u : 0u), src);
             float2 acc[K::NE / 2];
-            row_warp<K>(p, rs, rl, lc, acc, lane);
+            if constexpr (K::STAGED) row_warp_staged<K>(p, rs, rl, lc, acc, lane, sbase);
+            else row_warp<K>(p, rs, rl, lc, acc, lane);
             if (flags & 1u) {
                 piece_row<K>(p, i, j, gc, (int64_t)rb + src, (flags & 2u) != 0, acc, lc, lane);
             } else if (g == 0) {
@@ -424,6 +513,8 @@ spmm_csr_persistent(const Problem p, int flags) {
     using K = KCfg<TA, TB, LPN, VPL>;
     const int lane = threadIdx.x & 31;
     const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(spmm_dyn_smem) +
+                           (uint32_t)((threadIdx.x >> 5) * K::STAGE_BYTES + lane * 16);
     const int T = p.TR * p.TC;
     const int home = ((flags & kFlagWarpHome) ? warp : (int)blockIdx.x) % T;
     for (int step = 0; step < T; ++step) {
@@ -448,7 +539,7 @@ spmm_csr_persistent(const Problem p, int flags) {
             if (lane == 0) c = atomicAdd(p.tile_ctr + tid, 1);
             c = __shfl_sync(kFull, c, 0);
             if (c >= nch) break;
-            process_unit<K>(p, i, j, c, lc, ls, lane);
+            process_unit<K>(p, i, j, c, lc, ls, lane, sbase);
         }
     }
 }

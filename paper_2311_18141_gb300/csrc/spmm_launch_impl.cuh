@@ -11,8 +11,12 @@ template <class TA, class TB, int LPN, int VPL>
 cudaError_t launch_one(const Problem& p, const LaunchOpts& o, cudaStream_t s) {
     auto kern = spmm_csr_persistent<TA, TB, LPN, VPL>;
     const int threads = o.warps_per_cta * 32;
+    const size_t smem = (size_t)o.warps_per_cta * KCfg<TA, TB, LPN, VPL>::STAGE_BYTES;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     if (o.ctas_per_sm > 0 && o.ctas_per_sm < per_sm) per_sm = o.ctas_per_sm;
@@ -20,7 +24,7 @@ cudaError_t launch_one(const Problem& p, const LaunchOpts& o, cudaStream_t s) {
     const int64_t need = (o.units + o.warps_per_cta - 1) / o.warps_per_cta;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    kern<<<(unsigned)grid, threads, 0, s>>>(p, o.flags);
+    kern<<<(unsigned)grid, threads, smem, s>>>(p, o.flags);
     return cudaGetLastError();
 }
 
@@ -43,8 +47,12 @@ cudaError_t launch_batched(const BatchEntry* table, const int64_t* item_base, in
                            int* counter, int64_t max_items, int ctas_per_sm, cudaStream_t s) {
     auto kern = spmm_csr_batched_kernel<TA, TB>;
     const int threads = kBatchWarps * 32;
+    const size_t smem = (size_t)kBatchWarps * batch_stage_bytes<TA, TB>();
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
@@ -52,7 +60,7 @@ cudaError_t launch_batched(const BatchEntry* table, const int64_t* item_base, in
     const int64_t need = (max_items + kBatchWarps - 1) / kBatchWarps;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    kern<<<(unsigned)grid, threads, 0, s>>>(table, item_base, count, ws, counter);
+    kern<<<(unsigned)grid, threads, smem, s>>>(table, item_base, count, ws, counter);
     return cudaGetLastError();
 }
 
