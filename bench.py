@@ -251,8 +251,8 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     binding.load_library()
     TR, TC = (int(x) for x in args.grid.split("x"))
-    if args.order < 0 or args.order > 3:
-        raise SystemExit("--order is 0..3")
+    if args.order < 0 or args.order > 7:
+        raise SystemExit("--order is 0..7")
     A, B = make_workload(args.scale, args.n, dev)
     M, K, N, nnz = A.M, A.K, args.n, A.nnz
     C = torch.empty(M, N, device=dev)

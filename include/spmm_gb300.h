@@ -72,7 +72,10 @@ typedef struct spmm_tuning {
     int32_t warps_per_cta; /* 4 or 8                                                  */
     int32_t ctas_per_sm;   /* persistent CTAs per SM; 0 = as many as fit              */
     int32_t tile_order;    /* bit 0: steal along the tile column first (else the row);
-                              bit 1: stagger home tiles per warp (else per CTA)       */
+                              bit 1: stagger home tiles per warp (else per CTA);
+                              bit 2: column sweep -- every CTA starts in column block 0
+                              and steals column-major, so one column block of B is
+                              live at a time                                           */
     int32_t reserved[4];
 } spmm_tuning;
 

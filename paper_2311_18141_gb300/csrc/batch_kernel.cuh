@@ -38,9 +38,10 @@ constexpr int kBatchWarps = 8;
 // Staging bytes per warp: the largest of the five shapes.
 template <class TA, class TB>
 __host__ __device__ constexpr int batch_stage_bytes() {
-    constexpr int a = KCfg<TA, TB, 2, 1>::STAGE_BYTES, b = KCfg<TA, TB, 4, 1>::STAGE_BYTES;
-    constexpr int c = KCfg<TA, TB, 8, 1>::STAGE_BYTES;
-    return a > b ? (a > c ? a : c) : (b > c ? b : c);
+    // stages hold at most 8 steps of one vector, so the widest shapes set the size
+    return KCfg<TA, TB, 32, 1>::STAGE_BYTES > KCfg<TA, TB, 8, 1>::STAGE_BYTES
+               ? KCfg<TA, TB, 32, 1>::STAGE_BYTES
+               : KCfg<TA, TB, 8, 1>::STAGE_BYTES;
 }
 
 template <class TA, class TB, int LPN>

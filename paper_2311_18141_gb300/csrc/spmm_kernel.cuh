@@ -35,7 +35,10 @@
 #define SPMM_LONG_UNROLL 4 // B gathers in flight per lane on the whole-warp path
 #endif
 #ifndef SPMM_STAGE
-#define SPMM_STAGE 1       // stage whole-warp gathers through shared memory (groups <= 8 lanes)
+#define SPMM_STAGE 1       // stage whole-warp gathers through shared memory
+#endif
+#ifndef SPMM_STAGE_SHORT
+#define SPMM_STAGE_SHORT 0 // stage short-row gathers too (slower on power-law rows)
 #endif
 
 namespace spmm {
@@ -43,6 +46,8 @@ namespace spmm {
 // Launch flags of the persistent kernel.
 constexpr int kFlagOrderColumn = 1;   // steal along the tile column first
 constexpr int kFlagWarpHome = 2;      // stagger home tiles per warp instead of per CTA
+constexpr int kFlagSweep = 4;         // all CTAs start in column block 0, steal column-major:
+                                      // one column block's B rows are live in L2 at a time
 
 template <typename TA_, typename TB_, int LPN_, int VPL_>
 struct KCfg {
@@ -66,11 +71,16 @@ struct KCfg {
     static constexpr int RPP = 32 / SUB;
     static constexpr int NS = VPS * EPV;                       // short-path floats per lane
     static constexpr int SHORT_MAX = 16;                       // longer rows: whole warp
-    // Whole-warp gathers staged through shared memory with cp.async, two
-    // 32-nonzero batches in flight per warp (each lane LPN 16-byte slots per
-    // batch); used when a group is at most 8 lanes wide and one vector deep.
-    static constexpr bool STAGED = SPMM_STAGE && LPN <= 8 && VPL == 1;
-    static constexpr int STAGE_BYTES = STAGED ? 2 * LPN * 32 * 16 : 0;   // per warp
+    // Whole-warp gathers staged through shared memory with cp.async: a stage
+    // is SS steps of a 32-nonzero batch (SS*VPL 16-byte slots per lane), two
+    // stages in flight per warp.
+    static constexpr bool STAGED = SPMM_STAGE != 0;
+    static constexpr int SS = (8 / VPL) < LPN ? (8 / VPL) : LPN;   // steps per stage
+    static constexpr int SPB = LPN / SS;                           // stages per batch
+    static constexpr int STAGE_BYTES0 = 2 * SS * VPL * 32 * 16;   // whole-warp path
+    static constexpr int STAGE_BYTES1 = 2 * VPS * 32 * 16;        // short-row path
+    static constexpr int STAGE_BYTES =
+        STAGED ? (STAGE_BYTES0 > STAGE_BYTES1 ? STAGE_BYTES0 : STAGE_BYTES1) : 0;   // per warp
 };
 
 // Dynamic shared memory of the persistent kernels (staging buffers).
@@ -310,72 +320,84 @@ __device__ __forceinline__ void row_warp(const Problem& p, int rs, int L,
         }
 }
 
-// The whole-warp walk with shared-memory staging.  Batch b's gathers are
-// issued as 16-byte cp.async copies into stage b&1 while batch b-1 is summed
-// from the other stage.  Lane l issues and later reads its own slots only, so
-// cp.async.wait_group alone orders the copy before the read.  Slots of padding
-// lanes are zero-filled and their values are 0, so no step needs a predicate.
-// `sbase` is this lane's first slot: warp region + lane * 16 bytes.
+// The whole-warp walk with shared-memory staging.  The row's 32-nonzero
+// batches are cut into stages of SS steps; stage t+1's gathers are issued as
+// 16-byte cp.async copies into buffer (t+1)&1 while stage t is summed from the
+// other buffer.  Lane l issues and later reads its own slots only, so
+// cp.async.wait_group alone orders copy and read.  Slots of padding lanes are
+// zero-filled and their values are 0, so no step needs a predicate.  `sbase`
+// is this lane's first slot: warp region + lane * 16 bytes.
 template <class K>
 __device__ __forceinline__ void row_warp_staged(const Problem& p, int rs, int L,
-                                                const LaneCols<1>& lc, float2* acc, int lane,
-                                                uint32_t sbase) {
+                                                const LaneCols<K::VPL>& lc, float2* acc,
+                                                int lane, uint32_t sbase) {
     const int g = lane / K::LPN;
+    constexpr uint32_t kStage = K::SS * K::VPL * 32 * 16;   // bytes of one buffer
 #pragma unroll
     for (int e = 0; e < K::NE / 2; ++e) acc[e] = make_float2(0.0f, 0.0f);
     const int nb = (L + 31) >> 5;
-    // registers of the batch being issued (col_i, val_i) and of the one after
-    int col_i = 0, col_n = 0;
-    float val_i = 0.0f, val_n = 0.0f;
+    const int nst = nb * K::SPB;
+    // column indices and values of the current batch (c) and of the next (n)
+    int col_c = 0, col_n = 0;
+    float val_c = 0.0f, val_n = 0.0f;
     if (lane < L) {
-        col_i = ld_stream_i32(p.colind + rs + lane);
-        val_i = aval<typename K::TA, true>(p.vals, (int64_t)rs + lane);
-        if (p.b_scale) val_i *= __ldg(p.b_scale + col_i);
+        col_c = ld_stream_i32(p.colind + rs + lane);
+        val_c = aval<typename K::TA, true>(p.vals, (int64_t)rs + lane);
+        if (p.b_scale) val_c *= __ldg(p.b_scale + col_c);
     }
     if (32 + lane < L) {
         col_n = ld_stream_i32(p.colind + rs + 32 + lane);
         val_n = aval<typename K::TA, true>(p.vals, (int64_t)rs + 32 + lane);
+        if (p.b_scale) val_n *= __ldg(p.b_scale + col_n);
     }
-    auto issue = [&](int b, int col) {
+    auto issue = [&](int t, int col) {
+        const int b = t / K::SPB, h = t - b * K::SPB;
         const int cnt = min(32, L - 32 * b);
-        const uint32_t st = sbase + (uint32_t)((b & 1) * K::LPN * 32 * 16);
+        const uint32_t buf = sbase + (uint32_t)(t & 1) * kStage;
 #pragma unroll
-        for (int s = 0; s < K::LPN; ++s) {
-            const int cc = __shfl_sync(kFull, col, s, K::LPN);
-            const int ok = (g * K::LPN + s < cnt) ? 16 : 0;
-            cp_async16(st + (uint32_t)(s * 32 * 16), brow(lc, cc), ok);
+        for (int s = 0; s < K::SS; ++s) {
+            const int step = h * K::SS + s;
+            const int cc = __shfl_sync(kFull, col, step, K::LPN);
+            const int ok = (g * K::LPN + step < cnt) ? 16 : 0;
+            const char* rp = brow(lc, cc);
+#pragma unroll
+            for (int q = 0; q < K::VPL; ++q)
+                cp_async16(buf + (uint32_t)((s * K::VPL + q) * 32 * 16), rp + lc.qoff[q], ok);
         }
         cp_async_commit();
     };
-    issue(0, col_i);
-    float val_c = val_i;   // values of the batch being summed
+    issue(0, col_c);
 #pragma unroll 1
-    for (int b = 0; b < nb; ++b) {
-        if (b + 1 < nb) {
-            if (p.b_scale && 32 * (b + 1) + lane < L) val_n *= __ldg(p.b_scale + col_n);
-            issue(b + 1, col_n);
-            const float val_next = val_n;
-            col_i = col_n;
-            val_i = val_next;
+    for (int t = 0; t < nst; ++t) {
+        const int b = t / K::SPB, h = t - b * K::SPB;
+        if (t + 1 < nst) {
+            issue(t + 1, (h + 1 < K::SPB) ? col_c : col_n);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        const uint32_t buf = sbase + (uint32_t)(t & 1) * kStage;
+#pragma unroll
+        for (int s = 0; s < K::SS; ++s) {
+            const float a = __shfl_sync(kFull, val_c, h * K::SS + s, K::LPN);
+            const float2 a2 = make_float2(a, a);
+#pragma unroll
+            for (int q = 0; q < K::VPL; ++q)
+                fma_vec<typename K::TB>(acc + q * (K::EPV / 2), a2,
+                                        lds128(buf + (uint32_t)((s * K::VPL + q) * 32 * 16)));
+        }
+        if (h == K::SPB - 1 && b + 1 < nb) {   // move on to batch b+1, fetch batch b+2
+            col_c = col_n;
+            val_c = val_n;
             col_n = 0;
             val_n = 0.0f;
             const int idx = 32 * (b + 2) + lane;
             if (idx < L) {
                 col_n = ld_stream_i32(p.colind + rs + idx);
                 val_n = aval<typename K::TA, true>(p.vals, (int64_t)rs + idx);
+                if (p.b_scale) val_n *= __ldg(p.b_scale + col_n);
             }
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
         }
-        const uint32_t st = sbase + (uint32_t)((b & 1) * K::LPN * 32 * 16);
-#pragma unroll
-        for (int s = 0; s < K::LPN; ++s) {
-            const float a = __shfl_sync(kFull, val_c, s, K::LPN);
-            const uint4 bv = lds128(st + (uint32_t)(s * 32 * 16));
-            fma_vec<typename K::TB>(acc, make_float2(a, a), bv);
-        }
-        val_c = val_i;
     }
 #pragma unroll
     for (int off = K::LPN; off < 32; off <<= 1)
@@ -386,11 +408,15 @@ __device__ __forceinline__ void row_warp_staged(const Problem& p, int rs, int L,
         }
 }
 
-// Short rows of the batch: SUB lanes per row, RPP rows per pass.  Each lane
-// fetches the next nonzero's column and value while gathering the current one.
+// Short rows of the batch: SUB lanes per row, RPP rows per pass; the next
+// column index and value are fetched one nonzero ahead.  With SPMM_STAGE_SHORT
+// the B vectors of nonzero k+1 are also copied into shared memory (cp.async,
+// zero-filled past the row's end) while nonzero k is summed.
 template <class K>
 __device__ __forceinline__ void short_rows(const Problem& p, int rb, unsigned smask, int s,
-                                           int L, const LaneCols<K::VPS>& ls, int lane) {
+                                           int L, const LaneCols<K::VPS>& ls, int lane,
+                                           uint32_t sbase) {
+    constexpr uint32_t kBuf = K::VPS * 32 * 16;   // one nonzero's slots for the warp
 #pragma unroll 1
     for (int pass = 0; pass < K::SUB; ++pass) {
         const unsigned pbits =
@@ -410,25 +436,70 @@ __device__ __forceinline__ void short_rows(const Problem& p, int rb, unsigned sm
         if (rl > 0) {
             c_n = __ldg(p.colind + rs);
             a_n = aval<typename K::TA, false>(p.vals, (int64_t)rs);
+            if (p.b_scale) a_n *= __ldg(p.b_scale + c_n);
         }
-#pragma unroll 1
-        for (int k = 0; k < lmax; ++k) {
-            const int c0 = c_n;
-            float a0 = a_n;
-            if (k + 1 < rl) {
-                c_n = __ldg(p.colind + rs + k + 1);
-                a_n = aval<typename K::TA, false>(p.vals, (int64_t)rs + k + 1);
-            }
-            if (k < rl) {
-                if (p.b_scale) a0 *= __ldg(p.b_scale + c0);
-                const char* r0 = brow(ls, c0);
-                uint4 b0[K::VPS];
-#pragma unroll
-                for (int v = 0; v < K::VPS; ++v) b0[v] = ld_b16(r0 + ls.qoff[v]);
-                const float2 a02 = make_float2(a0, a0);
+        if constexpr (K::STAGED && SPMM_STAGE_SHORT) {
+            auto issue = [&](int k, int col) {
+                const uint32_t buf = sbase + (uint32_t)(k & 1) * kBuf;
+                const char* r0 = brow(ls, col);
+                const int ok = (k < rl) ? 16 : 0;
 #pragma unroll
                 for (int v = 0; v < K::VPS; ++v)
-                    fma_vec<typename K::TB>(acc + v * (K::EPV / 2), a02, b0[v]);
+                    cp_async16(buf + (uint32_t)(v * 32 * 16), r0 + ls.qoff[v], ok);
+                cp_async_commit();
+            };
+            if (lmax > 0) issue(0, c_n);
+            float a_c = a_n;
+            c_n = 0;
+            a_n = 0.0f;
+            if (1 < rl) {
+                c_n = __ldg(p.colind + rs + 1);
+                a_n = aval<typename K::TA, false>(p.vals, (int64_t)rs + 1);
+                if (p.b_scale) a_n *= __ldg(p.b_scale + c_n);
+            }
+#pragma unroll 1
+            for (int k = 0; k < lmax; ++k) {
+                if (k + 1 < lmax) {
+                    issue(k + 1, c_n);
+                    cp_async_wait<1>();
+                } else {
+                    cp_async_wait<0>();
+                }
+                const uint32_t buf = sbase + (uint32_t)(k & 1) * kBuf;
+                const float2 a2 = make_float2(a_c, a_c);
+#pragma unroll
+                for (int v = 0; v < K::VPS; ++v)
+                    fma_vec<typename K::TB>(acc + v * (K::EPV / 2), a2,
+                                            lds128(buf + (uint32_t)(v * 32 * 16)));
+                a_c = a_n;
+                c_n = 0;
+                a_n = 0.0f;
+                if (k + 2 < rl) {
+                    c_n = __ldg(p.colind + rs + k + 2);
+                    a_n = aval<typename K::TA, false>(p.vals, (int64_t)rs + k + 2);
+                    if (p.b_scale) a_n *= __ldg(p.b_scale + c_n);
+                }
+            }
+        } else {
+#pragma unroll 1
+            for (int k = 0; k < lmax; ++k) {
+                const int c0 = c_n;
+                const float a0 = a_n;
+                if (k + 1 < rl) {
+                    c_n = __ldg(p.colind + rs + k + 1);
+                    a_n = aval<typename K::TA, false>(p.vals, (int64_t)rs + k + 1);
+                    if (p.b_scale) a_n *= __ldg(p.b_scale + c_n);
+                }
+                if (k < rl) {
+                    const char* r0 = brow(ls, c0);
+                    uint4 b0[K::VPS];
+#pragma unroll
+                    for (int v = 0; v < K::VPS; ++v) b0[v] = ld_b16(r0 + ls.qoff[v]);
+                    const float2 a02 = make_float2(a0, a0);
+#pragma unroll
+                    for (int v = 0; v < K::VPS; ++v)
+                        fma_vec<typename K::TB>(acc + v * (K::EPV / 2), a02, b0[v]);
+                }
             }
         }
         // an empty row with beta == 1 and no row scale leaves C unchanged
@@ -502,7 +573,7 @@ __device__ __forceinline__ void process_unit(const Problem& p, int i, int j, int
 
         // ---- short rows: SUB lanes per row, RPP rows per pass ----
         const unsigned smask = __ballot_sync(kFull, is_short);
-        if (smask) short_rows<K>(p, rb, smask, s, L, ls, lane);
+        if (smask) short_rows<K>(p, rb, smask, s, L, ls, lane, sbase);
     }
 }
 
@@ -516,12 +587,14 @@ spmm_csr_persistent(const Problem p, int flags) {
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(spmm_dyn_smem) +
                            (uint32_t)((threadIdx.x >> 5) * K::STAGE_BYTES + lane * 16);
     const int T = p.TR * p.TC;
-    const int home = ((flags & kFlagWarpHome) ? warp : (int)blockIdx.x) % T;
+    const bool sweep = (flags & kFlagSweep) != 0;
+    const int home = sweep ? (int)blockIdx.x % p.TR
+                           : ((flags & kFlagWarpHome) ? warp : (int)blockIdx.x) % T;
     for (int step = 0; step < T; ++step) {
         int t = home + step;
         if (t >= T) t -= T;
         int i, j;
-        if (flags & kFlagOrderColumn) {
+        if (sweep || (flags & kFlagOrderColumn)) {
             j = t / p.TR;
             i = t - j * p.TR;
         } else {

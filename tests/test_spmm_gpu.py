@@ -60,8 +60,9 @@ def test_widths(N):
     assert_close_rel(C.numpy(), ref, bound, TOL_F32, f"N={N}")
 
 
-@pytest.mark.parametrize("opts", [dict(warps_per_cta=4), dict(tile_order=1),
-                                  dict(plan=False), dict(warps_per_cta=4, tile_order=1)])
+@pytest.mark.parametrize("opts", [dict(warps_per_cta=4), dict(tile_order=1), dict(tile_order=2),
+                                  dict(tile_order=4), dict(plan=False),
+                                  dict(warps_per_cta=4, tile_order=5)])
 def test_launch_options(opts):
     A = inputs.rmat_csr(12, 8, seed=6)
     N = 32
