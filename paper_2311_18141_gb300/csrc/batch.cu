@@ -14,19 +14,21 @@ using namespace spmm;
 
 namespace {
 
-constexpr int32_t kBatchMinChunk = 512;   // smallest chunk the autotuner may choose
+constexpr int32_t kBatchMinChunk = 256;   // smallest sub-chunk the autotuner may choose
 constexpr int32_t kBatchMaxTC = 2;        // widest column split the autotuner may choose
 
 size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 
-// item_base[q+1] = item_base[q] + chunks(q) * TC(q), read from each plan.
+// item_base[q+1] = item_base[q] + units(q) * TC(q), a unit being G = 32/lpn
+// sub-chunks of the plan.
 __global__ void item_base_kernel(const BatchEntry* table, int count, int64_t* item_base) {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
     int64_t run = 0;
     item_base[0] = 0;
     for (int q = 0; q < count; ++q) {
         const Problem& p = table[q].p;
-        run += (int64_t)p.blk_base[p.TR] * p.TC;
+        const int G = 32 / table[q].lpn;
+        run += (int64_t)((p.blk_base[p.TR] + G - 1) / G) * p.TC;
         item_base[q + 1] = run;
     }
 }
@@ -205,7 +207,12 @@ int spmm_batch_create(spmm_batch* out, const spmm_problem* problems, int32_t cou
         int32_t tc = P.tile_cols > 0 ? P.tile_cols : 1;
         while (shape_lpn(P.N, tc, b_dtype) == 0 && tc < 4096) tc *= 2;   // fit one warp
         b->TC[k] = tc;
-        b->D[k] = P.chunk_items > 0 ? P.chunk_items : 1024;
+        // default sub-chunk: a unit (32/lpn sub-chunks) of about 4096 items
+        const int32_t lpn = shape_lpn(P.N, tc, b_dtype);
+        const int32_t groups = lpn > 0 ? 32 / lpn : 1;
+        b->D[k] = P.chunk_items > 0 ? P.chunk_items
+                                    : std::min<int32_t>(2048, std::max<int32_t>(kBatchMinChunk,
+                                                                               4096 / groups));
     }
     const int st = batch_build(b, (cudaStream_t)stream);
     if (st) {
@@ -364,7 +371,7 @@ extern "C" int spmm_batch_autotune(spmm_batch b, void* workspace, size_t workspa
     if (st) return st;
     const int32_t tr_c[] = {1, 4};
     const int32_t tc_c[] = {1, 2};
-    const int32_t d_c[] = {kBatchMinChunk, 1024, 2048, 4096};
+    const int32_t d_c[] = {kBatchMinChunk, 512, 1024, 2048};
     for (int c = 0; c < (int)keys.size(); ++c) {
         int32_t bt = -1, bc = -1, bd = -1;
         for (int k = 0; k < b->count; ++k)

@@ -1,10 +1,11 @@
 // Batched persistent SpMM: many independent products C_p = beta_p*C_p + A_p*B_p
 // in one launch.
 //
-// Every problem keeps its own merge-path plan.  Its work units (chunk, column
-// block) are numbered after those of the problems before it (item_base), and
-// the warps of one persistent grid reserve items from a single global counter
-// with atomicAdd (Algorithm 3's fetch-and-add, over the whole batch): a warp
+// Every problem keeps its own merge-path plan.  Its work units (G consecutive
+// sub-chunks, column block) are numbered after those of the problems before it
+// (item_base), and the warps of one persistent grid reserve items from a single
+// global counter with atomicAdd (Algorithm 3's fetch-and-add, over the whole
+// batch): a warp
 // that finishes a small problem moves straight on to the next item of any
 // problem.  The host orders problems by decreasing work, so the largest are
 // reserved first.  Each warp copies the descriptor of the problem it is working
@@ -35,22 +36,34 @@ static_assert(sizeof(BatchEntry) % 4 == 0, "descriptor copied as 32-bit words");
 
 constexpr int kBatchWarps = 8;
 
-// Staging bytes per warp: the largest of the five shapes.
+// Staging bytes per warp: the largest of the five shapes (all have VPL = 1,
+// so a stage holds at most 8 items of one vector per lane).
 template <class TA, class TB>
 __host__ __device__ constexpr int batch_stage_bytes() {
-    // stages hold at most 8 steps of one vector, so the widest shapes set the size
-    return KCfg<TA, TB, 32, 1>::STAGE_BYTES > KCfg<TA, TB, 8, 1>::STAGE_BYTES
+    return KCfg<TA, TB, 32, 1>::STAGE_BYTES > KCfg<TA, TB, 2, 1>::STAGE_BYTES
                ? KCfg<TA, TB, 32, 1>::STAGE_BYTES
-               : KCfg<TA, TB, 8, 1>::STAGE_BYTES;
+               : KCfg<TA, TB, 2, 1>::STAGE_BYTES;
 }
 
+// Unit u of a problem in column block j: its sub-chunks u*G .. u*G+G-1, counted
+// over all row blocks, one per lane group; each group finds its own row block.
 template <class TA, class TB, int LPN>
-__device__ __forceinline__ void batch_unit(const Problem& p, int i, int j, int c, int lane,
+__device__ __forceinline__ void batch_unit(const Problem& p, int u, int j, int lane,
                                            uint32_t sbase) {
     using K = KCfg<TA, TB, LPN, 1>;
     const LaneCols<K::VPL> lc = lane_cols<K, K::VPL, K::LPN>(p, j, lane % K::LPN);
-    const LaneCols<K::VPS> ls = lane_cols<K, K::VPS, K::SUB>(p, j, lane % K::SUB);
-    process_unit<K>(p, i, j, c, lc, ls, lane, sbase);
+    const int gsc = u * K::G + lane / K::LPN;
+    int il = 0, cs = -1;
+    if (gsc < p.blk_base[p.TR]) {
+        int ih = p.TR - 1;   // largest il with blk_base[il] <= gsc
+        while (il < ih) {
+            const int mid = (il + ih + 1) >> 1;
+            if (p.blk_base[mid] <= gsc) il = mid;
+            else ih = mid - 1;
+        }
+        cs = gsc - p.blk_base[il];
+    }
+    walk_unit<K>(p, il, j, cs, lc, lane, sbase);
 }
 
 template <class TA, class TB>
@@ -94,22 +107,14 @@ spmm_csr_batched_kernel(const BatchEntry* __restrict__ table,
         }
         const Problem& p = sp[w];
         const int local = item - (int)item_base[lo];
-        const int gcl = local / p.TC;
-        const int j = local - gcl * p.TC;
-        // row block of the chunk: largest i with blk_base[i] <= gcl
-        int il = 0, ih = p.TR - 1;
-        while (il < ih) {
-            const int mid = (il + ih + 1) >> 1;
-            if (p.blk_base[mid] <= gcl) il = mid;
-            else ih = mid - 1;
-        }
-        const int c = gcl - p.blk_base[il];
+        const int u = local / p.TC;
+        const int j = local - u * p.TC;
         switch (e->lpn) {
-            case 2: batch_unit<TA, TB, 2>(p, il, j, c, lane, sbase); break;
-            case 4: batch_unit<TA, TB, 4>(p, il, j, c, lane, sbase); break;
-            case 8: batch_unit<TA, TB, 8>(p, il, j, c, lane, sbase); break;
-            case 16: batch_unit<TA, TB, 16>(p, il, j, c, lane, sbase); break;
-            default: batch_unit<TA, TB, 32>(p, il, j, c, lane, sbase); break;
+            case 2: batch_unit<TA, TB, 2>(p, u, j, lane, sbase); break;
+            case 4: batch_unit<TA, TB, 4>(p, u, j, lane, sbase); break;
+            case 8: batch_unit<TA, TB, 8>(p, u, j, lane, sbase); break;
+            case 16: batch_unit<TA, TB, 16>(p, u, j, lane, sbase); break;
+            default: batch_unit<TA, TB, 32>(p, u, j, lane, sbase); break;
         }
     }
 }

@@ -38,11 +38,21 @@ __device__ __forceinline__ uint4 ld_b16(const void* p) {
     return __ldg(reinterpret_cast<const uint4*>(p));
 }
 
-// 16-byte asynchronous copy global -> shared (L1-allocating); copies
-// `src_bytes` (16 or 0) and zero-fills the rest of the 16 bytes.
+// 16-byte asynchronous copy global -> shared; copies `src_bytes` (16 or 0)
+// and zero-fills the rest of the 16 bytes.  SPMM_CP_ASYNC_CA=1 allocates the
+// line in L1 (.ca); the default bypasses L1 (.cg): gathered B rows are
+// rarely re-read from the same SM.
+#ifndef SPMM_CP_ASYNC_CA
+#define SPMM_CP_ASYNC_CA 0
+#endif
 __device__ __forceinline__ void cp_async16(uint32_t smem_addr, const void* gptr, int src_bytes) {
+#if SPMM_CP_ASYNC_CA
     asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;"
                  :: "r"(smem_addr), "l"(gptr), "r"(src_bytes) : "memory");
+#else
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;"
+                 :: "r"(smem_addr), "l"(gptr), "r"(src_bytes) : "memory");
+#endif
 }
 __device__ __forceinline__ void cp_async_commit() {
     asm volatile("cp.async.commit_group;" ::: "memory");

@@ -85,15 +85,16 @@ __global__ void plan_bounds_kernel(const int32_t* __restrict__ rowptr, int M, in
         if (rowend <= d - mid - 1) xl = mid + 1;
         else xh = mid;
     }
-    // A boundary inside a light row (fewer than D/2 items) moves to that row's
-    // start, so only heavy rows are ever cut between chunks.  The moved
-    // boundary stays on the merge path, moves back by less than D/2, and
-    // boundaries inside heavy rows stay on exact diagonals.
+    // A boundary inside a light row (fewer than D/8 items) moves to that row's
+    // start, so only rows of D/8 items or more are ever cut between chunks.
+    // The moved boundary stays on the merge path and moves back by less than
+    // D/8 (chunks stay within 1/8 of D), and boundaries inside heavier rows
+    // stay on exact diagonals.
     int64_t y = d - xl;
     if (xl < R) {
         const int64_t rs = (int64_t)rowptr[row_lo + xl] - nnz_lo;
         const int64_t re = (int64_t)rowptr[row_lo + xl + 1] - nnz_lo;
-        if (y > rs && 2 * (re - rs + 1) < D) y = rs;
+        if (y > rs && 8 * (re - rs + 1) < D) y = rs;
     }
     bnd_row[b] = (int32_t)(row_lo + xl);
     bnd_nnz[b] = (int32_t)(nnz_lo + y);
@@ -105,13 +106,24 @@ int64_t plan_chunk_cap(int64_t M, int64_t nnz, int32_t TR, int32_t D) {
     return ceil_div(M + nnz, D) + TR;
 }
 
-int32_t plan_default_chunk(int64_t M, int64_t nnz, int32_t TC, int sms) {
+int32_t plan_default_chunk(int64_t M, int64_t nnz, int32_t TC, int sms, int groups) {
     const int64_t nwarps = (int64_t)(sms > 0 ? sms : 148) * 32;
-    int64_t d = ceil_div((M + nnz) * (int64_t)TC, 16 * nwarps);
-    if (d < 256) d = 256;
+    if (groups < 1) groups = 1;
+    // about 16 units per warp of the full grid, a unit being `groups` chunks
+    int64_t d = ceil_div((M + nnz) * (int64_t)TC, 16 * nwarps * groups);
+    if (d < 128) d = 128;
     if (d > 16384) d = 16384;
     d = ceil_div(d, 32) * 32;
     return (int32_t)d;
+}
+
+int plan_default_groups(int64_t N, int32_t TC) {
+    if (TC < 1) TC = 1;
+    const int64_t nvec = ((N + TC - 1) / TC + 3) / 4;   // FP32 vectors of a column block
+    if (nvec >= 32) return 1;
+    int lpn = 2;
+    while (lpn < nvec) lpn <<= 1;
+    return 32 / lpn;
 }
 
 size_t plan_array_bytes(int32_t TR, int64_t cap) {

@@ -241,7 +241,7 @@ extern "C" int spmm_sddmm_csr(const int32_t* A_rowptr, const int32_t* A_colind, 
     } else {
         TR = 1; TC = 1;
         RB = (int32_t)M;
-        D = plan_default_chunk(M, nnz, 1, device_sm_count());
+        D = plan_default_chunk(M, nnz, 1, device_sm_count(), 1);
         cap = plan_chunk_cap(M, nnz, TR, D);
         // layout [status, counter (256 B)][plan arrays]
         const size_t pb = plan_array_bytes(TR, cap);

@@ -21,7 +21,10 @@ cudaError_t launch_one(const Problem& p, const LaunchOpts& o, cudaStream_t s) {
     if (per_sm < 1) per_sm = 1;
     if (o.ctas_per_sm > 0 && o.ctas_per_sm < per_sm) per_sm = o.ctas_per_sm;
     int64_t grid = (int64_t)device_sm_count() * per_sm;
-    const int64_t need = (o.units + o.warps_per_cta - 1) / o.warps_per_cta;
+    // o.units counts plan chunks; a warp's unit is G of them
+    constexpr int G = KCfg<TA, TB, LPN, VPL>::G;
+    const int64_t warp_units = (o.units + G - 1) / G;
+    const int64_t need = (warp_units + o.warps_per_cta - 1) / o.warps_per_cta;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
     kern<<<(unsigned)grid, threads, smem, s>>>(p, o.flags);
