@@ -251,8 +251,8 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     binding.load_library()
     TR, TC = (int(x) for x in args.grid.split("x"))
-    if args.order < 0 or args.order > 7:
-        raise SystemExit("--order is 0..7")
+    if args.order < 0 or args.order > 15:
+        raise SystemExit("--order is 0..15")
     A, B = make_workload(args.scale, args.n, dev)
     M, K, N, nnz = A.M, A.K, args.n, A.nnz
     C = torch.empty(M, N, device=dev)
@@ -351,7 +351,7 @@ def run_ours(args):
             "config": {"workload": WORKLOAD if (args.scale, N, args.grid) == (22, 128, "16x4")
                        else f"rmat-s{args.scale}-ef16-n{N}-fp32-grid{args.grid}",
                        "M": M, "K": K, "N": N, "nnz": nnz, "tile_grid": args.grid,
-                       "chunks": chunks, "work_units": units,
+                       "chunks": chunks, "work_units": units, "tile_order": args.order,
                        "parallelism": f"replicas x{world}" if world > 1 else "1 gpu",
                        "l2": "inputs larger than L2 (A+B+C = %.2f GB per step)" % (algo_bytes / 1e9)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -68,14 +68,18 @@ typedef struct spmm_plan_s* spmm_plan;
 
 /* Tuning knobs; a zero field means "library default".  Host struct. */
 typedef struct spmm_tuning {
-    int32_t chunk_items;   /* merge-path items (rows + nonzeros) per work unit        */
+    int32_t chunk_items;   /* merge-path items (rows + nonzeros) per plan chunk; a
+                              warp's work unit is 32/LPN chunks, one per lane group     */
     int32_t warps_per_cta; /* 4 or 8                                                  */
     int32_t ctas_per_sm;   /* persistent CTAs per SM; 0 = as many as fit              */
     int32_t tile_order;    /* bit 0: steal along the tile column first (else the row);
                               bit 1: stagger home tiles per warp (else per CTA);
                               bit 2: column sweep -- every CTA starts in column block 0
                               and steals column-major, so one column block of B is
-                              live at a time                                           */
+                              live at a time;
+                              bit 3: lockstep -- every warp starts on tile 0 and visits
+                              the tiles in the same order (bit 0 picks column-major),
+                              so one tile's B rows are live at a time                   */
     int32_t reserved[4];
 } spmm_tuning;
 

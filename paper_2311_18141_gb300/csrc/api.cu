@@ -61,7 +61,7 @@ void resolve_tuning(const spmm_tuning* in, spmm_tuning* out) {
     if (in) *out = *in;
     if (out->warps_per_cta != 4 && out->warps_per_cta != 8) out->warps_per_cta = 8;
     if (out->ctas_per_sm < 0) out->ctas_per_sm = 0;
-    if (out->tile_order < 0 || out->tile_order > 7) out->tile_order = 0;
+    if (out->tile_order < 0 || out->tile_order > 15) out->tile_order = 0;
     if (out->chunk_items < 0) out->chunk_items = 0;
 }
 
@@ -262,6 +262,7 @@ int spmm_csr(const int32_t* A_rowptr, const int32_t* A_colind, const void* A_val
     if (workspace_bytes < sc.total) return SPMM_ERR_WORKSPACE;
 
     Problem p;
+    memset(&p, 0, sizeof(p));
     p.rowptr = A_rowptr; p.colind = A_colind; p.vals = A_vals; p.a_scale = A_row_scale;
     p.B = B; p.b_scale = B_row_scale; p.C = C; p.ldb = ldb; p.ldc = ldc;
     p.M = (int32_t)M; p.N = (int32_t)N; p.a_dtype = a_dtype; p.beta = beta;

@@ -36,8 +36,8 @@ static_assert(sizeof(BatchEntry) % 4 == 0, "descriptor copied as 32-bit words");
 
 constexpr int kBatchWarps = 8;
 
-// Staging bytes per warp: the largest of the five shapes (all have VPL = 1,
-// so a stage holds at most 8 items of one vector per lane).
+// Staging bytes per warp: the largest of the five shapes (VPL = 1; the
+// shapes with LPN < 8 stage whole 8-item batches).
 template <class TA, class TB>
 __host__ __device__ constexpr int batch_stage_bytes() {
     return KCfg<TA, TB, 32, 1>::STAGE_BYTES > KCfg<TA, TB, 2, 1>::STAGE_BYTES
@@ -48,8 +48,8 @@ __host__ __device__ constexpr int batch_stage_bytes() {
 // Unit u of a problem in column block j: its sub-chunks u*G .. u*G+G-1, counted
 // over all row blocks, one per lane group; each group finds its own row block.
 template <class TA, class TB, int LPN>
-__device__ __forceinline__ void batch_unit(const Problem& p, int u, int j, int lane,
-                                           uint32_t sbase) {
+__device__ __forceinline__ bool batch_unit(const Problem& p, int u, int j, int lane,
+                                           uint32_t wbase, uint32_t bar0, uint32_t& phases) {
     using K = KCfg<TA, TB, LPN, 1>;
     const LaneCols<K::VPL> lc = lane_cols<K, K::VPL, K::LPN>(p, j, lane % K::LPN);
     const int gsc = u * K::G + lane / K::LPN;
@@ -63,7 +63,7 @@ __device__ __forceinline__ void batch_unit(const Problem& p, int u, int j, int l
         }
         cs = gsc - p.blk_base[il];
     }
-    walk_unit<K>(p, il, j, cs, lc, lane, sbase);
+    return walk_unit<K>(p, il, j, cs, lc, lane, wbase, bar0, phases);
 }
 
 template <class TA, class TB>
@@ -74,8 +74,8 @@ spmm_csr_batched_kernel(const BatchEntry* __restrict__ table,
     __shared__ Problem sp[kBatchWarps];
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
-    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(spmm_dyn_smem) +
-                           (uint32_t)(w * batch_stage_bytes<TA, TB>() + lane * 16);
+    uint32_t bar0 = 0, phases = 0;
+    const uint32_t wbase = warp_staging<KCfg<TA, TB, 32, 1>>(lane, bar0);
     const int64_t total = item_base[count];
     int cur = -1;   // problem whose descriptor is in sp[w]
     while (true) {
@@ -109,13 +109,15 @@ spmm_csr_batched_kernel(const BatchEntry* __restrict__ table,
         const int local = item - (int)item_base[lo];
         const int u = local / p.TC;
         const int j = local - u * p.TC;
+        bool ok;
         switch (e->lpn) {
-            case 2: batch_unit<TA, TB, 2>(p, u, j, lane, sbase); break;
-            case 4: batch_unit<TA, TB, 4>(p, u, j, lane, sbase); break;
-            case 8: batch_unit<TA, TB, 8>(p, u, j, lane, sbase); break;
-            case 16: batch_unit<TA, TB, 16>(p, u, j, lane, sbase); break;
-            default: batch_unit<TA, TB, 32>(p, u, j, lane, sbase); break;
+            case 2: ok = batch_unit<TA, TB, 2>(p, u, j, lane, wbase, bar0, phases); break;
+            case 4: ok = batch_unit<TA, TB, 4>(p, u, j, lane, wbase, bar0, phases); break;
+            case 8: ok = batch_unit<TA, TB, 8>(p, u, j, lane, wbase, bar0, phases); break;
+            case 16: ok = batch_unit<TA, TB, 16>(p, u, j, lane, wbase, bar0, phases); break;
+            default: ok = batch_unit<TA, TB, 32>(p, u, j, lane, wbase, bar0, phases); break;
         }
+        if (!ok) return;
     }
 }
 

@@ -37,6 +37,19 @@
 #ifndef SPMM_MINBLOCKS
 #define SPMM_MINBLOCKS 3   // resident 256-thread CTAs per SM the register budget targets
 #endif
+#ifndef SPMM_MINBLOCKS_NARROW
+#define SPMM_MINBLOCKS_NARROW 3   // the same for shapes with LPN <= 8 and one vector per lane
+#endif
+#ifndef SPMM_NBUF
+#define SPMM_NBUF 2        // stage buffers per warp (stages in flight + 1)
+#endif
+#ifndef SPMM_STAGE_ITEMS
+#define SPMM_STAGE_ITEMS 8 // items per lane group in one stage (of one 16-byte vector each)
+#endif
+#ifndef SPMM_TMA
+#define SPMM_TMA 0         // 1: stage B rows with bulk copies on the TMA engine instead of
+                           // per-lane cp.async (correct, but slower for 128-512 byte rows)
+#endif
 
 namespace spmm {
 
@@ -45,6 +58,9 @@ constexpr int kFlagOrderColumn = 1;   // steal along the tile column first
 constexpr int kFlagWarpHome = 2;      // stagger home tiles per warp instead of per CTA
 constexpr int kFlagSweep = 4;         // all CTAs start in column block 0, steal column-major:
                                       // one column block's B rows are live in L2 at a time
+constexpr int kFlagLockstep = 8;      // all warps start on tile 0 and visit the tiles in the
+                                      // same order (row- or column-major by bit 0): one tile's
+                                      // B rows are live in L2 at a time
 
 template <typename TA_, typename TB_, int LPN_, int VPL_>
 struct KCfg {
@@ -60,11 +76,31 @@ struct KCfg {
     // how many of them each lane of the group holds
     static constexpr int MB = LPN < 8 ? 8 : LPN;
     static constexpr int IPL = MB / LPN;
-    // a stage is SS items (SS*VPL 16-byte slots per lane); two stages in flight
-    static constexpr int SS = (8 / VPL) < MB ? (8 / VPL) : MB;
+    // a stage is SS items (SS*VPL 16-byte slots per lane); NBUF stage
+    // buffers, NBUF-1 stages in flight while one is summed
+    // (a lane holding several items of a batch needs the batch in one stage)
+    static constexpr int SS0 = SPMM_STAGE_ITEMS / VPL < 1 ? 1 : SPMM_STAGE_ITEMS / VPL;
+    static constexpr int SS = (IPL > 1 || SS0 > MB) ? MB : SS0;
     static constexpr int SPB = MB / SS;                        // stages per decoded batch
-    static constexpr int STAGE_BYTES = 2 * SS * VPL * 32 * 16;  // per warp
+    // (shapes whose batch is a single stage keep two buffers of 8 items)
+    static constexpr int NBUF = SPB == 1 ? 2 : (SPMM_NBUF < 2 * SPB + 2 ? SPMM_NBUF : 2 * SPB + 1);
+    static constexpr int STAGE_BYTES = NBUF * SS * VPL * 32 * 16;  // per warp
+    // stage copies: bulk copies on the TMA engine (1) or 16-byte cp.async (0)
+    static constexpr bool TMA = SPMM_TMA != 0;
+    // resident CTAs per SM the register budget targets
+    static constexpr int MINB = (LPN <= 8 && VPL == 1) ? SPMM_MINBLOCKS_NARROW : SPMM_MINBLOCKS;
+    // the stage issued NBUF-1 stages ahead lies in a batch at most two past
+    // the current one (three batches are decoded at a time)
+    static_assert(NBUF >= 2 && NBUF < 2 * SPB + 2, "pipeline deeper than the decoded batches");
+    static_assert(!TMA || NBUF == 2, "bulk-copy staging uses two buffers");
+    static_assert(SPB == 1 || IPL == 1, "split batches need one item per lane");
 };
+
+// Dynamic shared memory of a persistent CTA of `warps` warps: a pair of
+// mbarriers (16 bytes) per warp, then the warps' staging regions.
+__host__ __device__ constexpr int smem_bytes(int warps, int stage_bytes) {
+    return warps * (16 + stage_bytes);
+}
 
 // Dynamic shared memory of the persistent kernels (staging buffers).
 extern __shared__ uint4 spmm_dyn_smem[];
@@ -258,10 +294,15 @@ __device__ __forceinline__ uint32_t group_or(uint32_t m, int g) {
 // ahead of use, so their column indices are in registers when their gathers
 // are issued, and the gathers of stage t+1 are in flight while stage t is
 // summed.
+//
+// `wbase` is the warp's staging region (two stage buffers); with bulk-copy
+// staging `bar0` is the warp's pair of mbarriers and `phases` their parity
+// bits, carried from unit to unit.  Returns false when a bounded wait ran out
+// (the status word then holds SPMM_ERR_TIMEOUT and the warp must stop).
 template <class K>
-__device__ __forceinline__ void walk_unit(const Problem& p, int i, int j, int cs,
+__device__ __forceinline__ bool walk_unit(const Problem& p, int i, int j, int cs,
                                           const LaneCols<K::VPL>& lc, int lane,
-                                          uint32_t sbase) {
+                                          uint32_t wbase, uint32_t bar0, uint32_t& phases) {
     constexpr int LPN = K::LPN, MB = K::MB, IPL = K::IPL, SS = K::SS, SPB = K::SPB;
     constexpr int VPL = K::VPL;
     constexpr uint32_t kStage = SS * VPL * 32 * 16;   // bytes of one stage buffer
@@ -357,9 +398,34 @@ __device__ __forceinline__ void walk_unit(const Problem& p, int i, int j, int cs
         }
     };
 
-    // gathers of stage t (items h*SS .. h*SS+SS-1 of a batch) into buffer t&1
-    auto issue = [&](int t, const ItemBatch<K>& X, int h) {
-        const uint32_t buf = sbase + (uint32_t)(t & 1) * kStage;
+    float2 acc[K::NE / 2];
+#pragma unroll
+    for (int q = 0; q < K::NE / 2; ++q) acc[q] = make_float2(0.0f, 0.0f);
+
+    // Accumulate item tt of a batch from its B vectors v[q]; a row-end item
+    // then writes its row (the tail piece: its slot).
+    auto take_item = [&](const ItemBatch<K>& X, int tt, float a, const uint4* v) {
+        const float2 a2 = make_float2(a, a);
+#pragma unroll
+        for (int q = 0; q < VPL; ++q) fma_vec<typename K::TB>(acc + q * (K::EPV / 2), a2, v[q]);
+        if ((X.ends >> tt) & 1u) {
+            const int row = X.rbase + __popc(X.ends & ((1u << tt) - 1u));
+            if (row == tail_row) store_slot<K>(p, 2 * (int64_t)gc, acc, lc);
+            else store_vecs<K, VPL, LPN>(p, row, acc, lc);
+#pragma unroll
+            for (int q = 0; q < K::NE / 2; ++q) acc[q] = make_float2(0.0f, 0.0f);
+        }
+    };
+    // value of item tt of stage h, from the lane that decoded it
+    auto item_val = [&](const ItemBatch<K>& X, int s, int h) -> float {
+        if constexpr (SPB == 1) return __shfl_sync(kFull, X.val[s / LPN], s % LPN, LPN);
+        else return __shfl_sync(kFull, X.val[0], h * SS + s, LPN);
+    };
+
+    // cp.async staging: slot (s, q) of lane l at buf + (s*VPL + q)*512 + l*16
+    // holds vector q of item s of the lane's group; padding slots are zeroed.
+    auto issue_lsu = [&](int t, const ItemBatch<K>& X, int h) {
+        const uint32_t buf = wbase + lane * 16 + (uint32_t)(t % K::NBUF) * kStage;
 #pragma unroll
         for (int s = 0; s < SS; ++s) {
             int tt, cc;
@@ -378,37 +444,67 @@ __device__ __forceinline__ void walk_unit(const Problem& p, int i, int j, int cs
         }
         cp_async_commit();
     };
-
-    float2 acc[K::NE / 2];
-#pragma unroll
-    for (int q = 0; q < K::NE / 2; ++q) acc[q] = make_float2(0.0f, 0.0f);
-    // sum stage t; a row-end item writes its row (the tail piece: its slot)
-    auto consume = [&](int t, const ItemBatch<K>& X, int h) {
-        const uint32_t buf = sbase + (uint32_t)(t & 1) * kStage;
+    auto consume_lsu = [&](int t, const ItemBatch<K>& X, int h) {
+        const uint32_t buf = wbase + lane * 16 + (uint32_t)(t % K::NBUF) * kStage;
 #pragma unroll
         for (int s = 0; s < SS; ++s) {
-            int tt;
-            float a;
-            if constexpr (SPB == 1) {
-                tt = s;
-                a = __shfl_sync(kFull, X.val[s / LPN], s % LPN, LPN);
-            } else {
-                tt = h * SS + s;
-                a = __shfl_sync(kFull, X.val[0], tt, LPN);
-            }
-            const float2 a2 = make_float2(a, a);
+            const int tt = SPB == 1 ? s : h * SS + s;
+            const float a = item_val(X, s, h);
+            uint4 v[VPL];
+#pragma unroll
+            for (int q = 0; q < VPL; ++q) v[q] = lds128(buf + (uint32_t)((s * VPL + q) * 32 * 16));
+            take_item(X, tt, a, v);
+        }
+    };
+
+    // Bulk-copy staging: the lane that decoded a nonzero item copies the
+    // item's whole column-block segment of its B row (cbytes) with one bulk
+    // copy to buf + (g*SS + s)*RBYTES; the stage's mbarrier counts the bytes.
+    constexpr uint32_t RBYTES = LPN * VPL * 16;
+    const char* bblk = reinterpret_cast<const char*>(p.B) + (int64_t)j * p.W * K::ESZ;
+    const uint32_t cbytes =
+        (uint32_t)(((int64_t)min(p.W, p.N - j * p.W) * K::ESZ + 15) & ~(int64_t)15);
+    auto issue_tma = [&](int t, const ItemBatch<K>& X, int h) {
+        const uint32_t b = (uint32_t)(t & 1);
+        const uint32_t buf = wbase + b * kStage + (uint32_t)(g * SS) * RBYTES;
+        const uint32_t bar = bar0 + 8u * b;
+        int mine = 0;
+#pragma unroll
+        for (int u = 0; u < IPL; ++u) {
+            const int s = tq + u * LPN - h * SS;
+            if ((SPB == 1 || (unsigned)s < (unsigned)SS) && ((X.nz >> (tq + u * LPN)) & 1u)) ++mine;
+        }
+        const int total = __reduce_add_sync(kFull, mine);
+        // the buffer's previous contents were read by this warp's shared loads
+        fence_proxy_async_smem();
+        if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)total * cbytes);
+        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < IPL; ++u) {
+            const int s = tq + u * LPN - h * SS;
+            if ((SPB == 1 || (unsigned)s < (unsigned)SS) && ((X.nz >> (tq + u * LPN)) & 1u))
+                bulk_g2s(buf + (uint32_t)s * RBYTES,
+                         bblk + (uint64_t)(uint32_t)X.col[u] * lc.ldb_bytes, cbytes, bar);
+        }
+    };
+    auto consume_tma = [&](int t, const ItemBatch<K>& X, int h) -> bool {
+        const uint32_t b = (uint32_t)(t & 1);
+        const bool ok = __all_sync(kFull, mbar_wait_bounded(bar0 + 8u * b, (phases >> b) & 1u));
+        phases ^= 1u << b;
+        if (!ok) return false;
+        const uint32_t buf = wbase + b * kStage + (uint32_t)(g * SS) * RBYTES + tq * 16;
+#pragma unroll
+        for (int s = 0; s < SS; ++s) {
+            const int tt = SPB == 1 ? s : h * SS + s;
+            const float a = item_val(X, s, h);
+            const bool live = (X.nz >> tt) & 1u;
+            uint4 v[VPL];
 #pragma unroll
             for (int q = 0; q < VPL; ++q)
-                fma_vec<typename K::TB>(acc + q * (K::EPV / 2), a2,
-                                        lds128(buf + (uint32_t)((s * VPL + q) * 32 * 16)));
-            if ((X.ends >> tt) & 1u) {
-                const int row = X.rbase + __popc(X.ends & ((1u << tt) - 1u));
-                if (row == tail_row) store_slot<K>(p, 2 * (int64_t)gc, acc, lc);
-                else store_vecs<K, VPL, LPN>(p, row, acc, lc);
-#pragma unroll
-                for (int q = 0; q < K::NE / 2; ++q) acc[q] = make_float2(0.0f, 0.0f);
-            }
+                v[q] = lds128_if(buf + (uint32_t)s * RBYTES + (uint32_t)(q * LPN * 16), live);
+            take_item(X, tt, a, v);
         }
+        return true;
     };
 
     const int nb = (__reduce_max_sync(kFull, nitems) + MB - 1) / MB;
@@ -417,18 +513,48 @@ __device__ __forceinline__ void walk_unit(const Problem& p, int i, int j, int cs
     decode(A);
     decode(B);
     decode(C);
-    if (nst > 0) issue(0, A, 0);
+    // stage t of the walk lies in batch t / SPB; batch b, b+1, b+2 are A, B, C
+    auto issue_lsu_stage = [&](int t, int b) {
+        const int bt = t / SPB;
+        const int ht = t - bt * SPB;
+        if (bt == b) issue_lsu(t, A, ht);
+        else if (bt == b + 1) issue_lsu(t, B, ht);
+        else issue_lsu(t, C, ht);
+    };
+    if constexpr (K::TMA) {
+        if (nst > 0) issue_tma(0, A, 0);
+    } else {
+#pragma unroll
+        for (int k = 0; k < K::NBUF - 1; ++k) {
+            if (k < nst) issue_lsu_stage(k, 0);
+            else cp_async_commit();   // empty group: the wait count stays NBUF-1
+        }
+    }
 #pragma unroll 1
     for (int t = 0; t < nst; ++t) {
         const int h = SPB == 1 ? 0 : (t & (SPB - 1));
-        if (t + 1 < nst) {
-            if (SPB > 1 && h + 1 < SPB) issue(t + 1, A, h + 1);
-            else issue(t + 1, B, 0);
-            cp_async_wait<1>();
+        if constexpr (K::TMA) {
+            if (t + 1 < nst) {
+                if (SPB > 1 && h + 1 < SPB) issue_tma(t + 1, A, h + 1);
+                else issue_tma(t + 1, B, 0);
+            }
+            if (!consume_tma(t, A, h)) {
+                // a bulk copy never arrived: report, wait (bounded) for the
+                // other stage still in flight, and stop this warp
+                if (lane == 0) atomicCAS(p.status, 0, SPMM_ERR_TIMEOUT);
+                if (t + 1 < nst) {
+                    const uint32_t b1 = (uint32_t)((t + 1) & 1);
+                    mbar_wait_bounded(bar0 + 8u * b1, (phases >> b1) & 1u);
+                }
+                return false;
+            }
         } else {
-            cp_async_wait<0>();
+            const int tn = t + K::NBUF - 1;
+            if (tn < nst) issue_lsu_stage(tn, t / SPB);
+            else cp_async_commit();
+            cp_async_wait<K::NBUF - 1>();
+            consume_lsu(t, A, h);
         }
-        consume(t, A, h);
         if (h == SPB - 1) {
             A = B;
             B = C;
@@ -437,22 +563,43 @@ __device__ __forceinline__ void walk_unit(const Problem& p, int i, int j, int cs
     }
     if (tail_row >= 0) piece_row<K>(p, i, j, gc, tail_row, true, nullptr, lc, tq, gmask, leader);
     if (head) piece_row<K>(p, i, j, gc, x1, false, acc, lc, tq, gmask, leader);
+    return true;
+}
+
+// Per-warp set-up of the staging region and its mbarriers; returns the
+// warp's staging base and sets bar0.
+template <class K>
+__device__ __forceinline__ uint32_t warp_staging(int lane, uint32_t& bar0) {
+    const int warps = blockDim.x >> 5;
+    const int w = threadIdx.x >> 5;
+    const uint32_t smem = (uint32_t)__cvta_generic_to_shared(spmm_dyn_smem);
+    bar0 = smem + (uint32_t)(w * 16);
+    if (K::TMA) {
+        if (lane == 0) {
+            mbar_init(bar0, 1);
+            mbar_init(bar0 + 8, 1);
+            mbar_init_fence();
+        }
+        __syncwarp();
+    }
+    return smem + (uint32_t)(warps * 16 + w * K::STAGE_BYTES);
 }
 
 // The persistent kernel: each warp is an independent worker.
 template <class TA, class TB, int LPN, int VPL>
-__global__ void __launch_bounds__(256, SPMM_MINBLOCKS)
+__global__ void __launch_bounds__(256, (KCfg<TA, TB, LPN, VPL>::MINB))
 spmm_csr_persistent(const Problem p, int flags) {
     using K = KCfg<TA, TB, LPN, VPL>;
     const int lane = threadIdx.x & 31;
     const int g = lane / K::LPN;
     const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(spmm_dyn_smem) +
-                           (uint32_t)((threadIdx.x >> 5) * K::STAGE_BYTES + lane * 16);
+    uint32_t bar0 = 0, phases = 0;
+    const uint32_t wbase = warp_staging<K>(lane, bar0);
     const int T = p.TR * p.TC;
     const bool sweep = (flags & kFlagSweep) != 0;
-    const int home = sweep ? (int)blockIdx.x % p.TR
-                           : ((flags & kFlagWarpHome) ? warp : (int)blockIdx.x) % T;
+    const int home = (flags & kFlagLockstep) ? 0
+                     : sweep ? (int)blockIdx.x % p.TR
+                             : ((flags & kFlagWarpHome) ? warp : (int)blockIdx.x) % T;
     for (int step = 0; step < T; ++step) {
         int t = home + step;
         if (t >= T) t -= T;
@@ -476,7 +623,8 @@ spmm_csr_persistent(const Problem p, int flags) {
             c = __shfl_sync(kFull, c, 0);
             if (c >= nun) break;
             const int cs = c * K::G + g;
-            walk_unit<K>(p, i, j, cs < nsub ? cs : -1, lc, lane, sbase);
+            if (!walk_unit<K>(p, i, j, cs < nsub ? cs : -1, lc, lane, wbase, bar0, phases))
+                return;
         }
     }
 }

@@ -11,7 +11,7 @@ template <class TA, class TB, int LPN, int VPL>
 cudaError_t launch_one(const Problem& p, const LaunchOpts& o, cudaStream_t s) {
     auto kern = spmm_csr_persistent<TA, TB, LPN, VPL>;
     const int threads = o.warps_per_cta * 32;
-    const size_t smem = (size_t)o.warps_per_cta * KCfg<TA, TB, LPN, VPL>::STAGE_BYTES;
+    const size_t smem = (size_t)smem_bytes(o.warps_per_cta, KCfg<TA, TB, LPN, VPL>::STAGE_BYTES);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
@@ -50,7 +50,7 @@ cudaError_t launch_batched(const BatchEntry* table, const int64_t* item_base, in
                            int* counter, int64_t max_items, int ctas_per_sm, cudaStream_t s) {
     auto kern = spmm_csr_batched_kernel<TA, TB>;
     const int threads = kBatchWarps * 32;
-    const size_t smem = (size_t)kBatchWarps * batch_stage_bytes<TA, TB>();
+    const size_t smem = (size_t)smem_bytes(kBatchWarps, batch_stage_bytes<TA, TB>());
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
