@@ -79,7 +79,10 @@ typedef struct spmm_tuning {
                               live at a time;
                               bit 3: lockstep -- every warp starts on tile 0 and visits
                               the tiles in the same order (bit 0 picks column-major),
-                              so one tile's B rows are live at a time                   */
+                              so one tile's B rows are live at a time;
+                              bit 4: interleave -- one queue per tile row hands out the
+                              same chunk of its tiles in turn (bit 3: all warps start
+                              on tile row 0)                                           */
     int32_t reserved[4];
 } spmm_tuning;
 

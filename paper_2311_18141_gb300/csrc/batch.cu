@@ -188,14 +188,18 @@ int spmm_batch_create(spmm_batch* out, const spmm_problem* problems, int32_t cou
     b->count = count;
     b->a_dtype = a_dtype;
     b->b_dtype = b_dtype;
-    // execution order: decreasing work (nonzeros x width, plus rows), ties by index
+    // execution order: by width (so the warps of an SM mostly run one kernel
+    // shape at a time), each width by decreasing work (nonzeros x width, plus
+    // rows), ties by index
     b->user_index.resize(count);
     std::iota(b->user_index.begin(), b->user_index.end(), 0);
     auto work = [&](int q) {
         return (double)(problems[q].nnz + problems[q].M) * (double)problems[q].N;
     };
-    std::stable_sort(b->user_index.begin(), b->user_index.end(),
-                     [&](int x, int y) { return work(x) > work(y); });
+    std::stable_sort(b->user_index.begin(), b->user_index.end(), [&](int x, int y) {
+        if (problems[x].N != problems[y].N) return problems[x].N > problems[y].N;
+        return work(x) > work(y);
+    });
     b->probs.resize(count);
     b->TR.resize(count);
     b->TC.resize(count);

@@ -17,7 +17,13 @@
 #include "spmm_kernel.cuh"
 
 #ifndef SPMM_BATCH_MINBLOCKS
-#define SPMM_BATCH_MINBLOCKS 2   // five inlined shapes need a larger register budget
+#define SPMM_BATCH_MINBLOCKS 2   // resident 256-thread CTAs per SM the register budget targets
+#endif
+#ifndef SPMM_BATCH_NBUF
+#define SPMM_BATCH_NBUF 2   // stage buffers per warp of the batched kernel
+#endif
+#ifndef SPMM_BATCH_UNIT_INLINE
+#define SPMM_BATCH_UNIT_INLINE __forceinline__   // or __noinline__: one function per shape
 #endif
 
 namespace spmm {
@@ -40,17 +46,19 @@ constexpr int kBatchWarps = 8;
 // shapes with LPN < 8 stage whole 8-item batches).
 template <class TA, class TB>
 __host__ __device__ constexpr int batch_stage_bytes() {
-    return KCfg<TA, TB, 32, 1>::STAGE_BYTES > KCfg<TA, TB, 2, 1>::STAGE_BYTES
-               ? KCfg<TA, TB, 32, 1>::STAGE_BYTES
-               : KCfg<TA, TB, 2, 1>::STAGE_BYTES;
+    return KCfg<TA, TB, 32, 1, SPMM_BATCH_NBUF>::STAGE_BYTES >
+                   KCfg<TA, TB, 2, 1, SPMM_BATCH_NBUF>::STAGE_BYTES
+               ? KCfg<TA, TB, 32, 1, SPMM_BATCH_NBUF>::STAGE_BYTES
+               : KCfg<TA, TB, 2, 1, SPMM_BATCH_NBUF>::STAGE_BYTES;
 }
 
 // Unit u of a problem in column block j: its sub-chunks u*G .. u*G+G-1, counted
 // over all row blocks, one per lane group; each group finds its own row block.
 template <class TA, class TB, int LPN>
-__device__ __forceinline__ bool batch_unit(const Problem& p, int u, int j, int lane,
-                                           uint32_t wbase, uint32_t bar0, uint32_t& phases) {
-    using K = KCfg<TA, TB, LPN, 1>;
+__device__ SPMM_BATCH_UNIT_INLINE bool batch_unit(const Problem& p, int u, int j, int lane,
+                                                  uint32_t wbase, uint32_t bar0,
+                                                  uint32_t& phases) {
+    using K = KCfg<TA, TB, LPN, 1, SPMM_BATCH_NBUF>;
     const LaneCols<K::VPL> lc = lane_cols<K, K::VPL, K::LPN>(p, j, lane % K::LPN);
     const int gsc = u * K::G + lane / K::LPN;
     int il = 0, cs = -1;
@@ -75,7 +83,8 @@ spmm_csr_batched_kernel(const BatchEntry* __restrict__ table,
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
     uint32_t bar0 = 0, phases = 0;
-    const uint32_t wbase = warp_staging<KCfg<TA, TB, 32, 1>>(lane, bar0);
+    const uint32_t wbase =
+        warp_staging<KCfg<TA, TB, 32, 1, SPMM_BATCH_NBUF>>(lane, bar0, batch_stage_bytes<TA, TB>());
     const int64_t total = item_base[count];
     int cur = -1;   // problem whose descriptor is in sp[w]
     while (true) {

@@ -61,8 +61,11 @@ constexpr int kFlagSweep = 4;         // all CTAs start in column block 0, steal
 constexpr int kFlagLockstep = 8;      // all warps start on tile 0 and visit the tiles in the
                                       // same order (row- or column-major by bit 0): one tile's
                                       // B rows are live in L2 at a time
+constexpr int kFlagInterleave = 16;   // one queue per tile row handing out the same chunk of
+                                      // its TC tiles in turn: warps that reserve one after the
+                                      // other read the same A chunk and the same B rows
 
-template <typename TA_, typename TB_, int LPN_, int VPL_>
+template <typename TA_, typename TB_, int LPN_, int VPL_, int NBUF_ = SPMM_NBUF>
 struct KCfg {
     using TA = TA_;
     using TB = TB_;
@@ -83,15 +86,18 @@ struct KCfg {
     static constexpr int SS = (IPL > 1 || SS0 > MB) ? MB : SS0;
     static constexpr int SPB = MB / SS;                        // stages per decoded batch
     // (shapes whose batch is a single stage keep two buffers of 8 items)
-    static constexpr int NBUF = SPB == 1 ? 2 : (SPMM_NBUF < 2 * SPB + 2 ? SPMM_NBUF : 2 * SPB + 1);
+    static constexpr int NBUF = NBUF_ < 2 ? 2 : NBUF_;
     static constexpr int STAGE_BYTES = NBUF * SS * VPL * 32 * 16;  // per warp
+    // the stage issued NBUF-1 stages ahead lies at most REL batches past the
+    // current one; one more batch is decoded so that its column indices load
+    // a batch before their gathers issue
+    static constexpr int REL = (SPB - 1 + NBUF - 1) / SPB;
+    static constexpr int DEPTH = REL + 2;
     // stage copies: bulk copies on the TMA engine (1) or 16-byte cp.async (0)
     static constexpr bool TMA = SPMM_TMA != 0;
     // resident CTAs per SM the register budget targets
     static constexpr int MINB = (LPN <= 8 && VPL == 1) ? SPMM_MINBLOCKS_NARROW : SPMM_MINBLOCKS;
-    // the stage issued NBUF-1 stages ahead lies in a batch at most two past
-    // the current one (three batches are decoded at a time)
-    static_assert(NBUF >= 2 && NBUF < 2 * SPB + 2, "pipeline deeper than the decoded batches");
+    static_assert(DEPTH <= 4, "at most four decoded batches");
     static_assert(!TMA || NBUF == 2, "bulk-copy staging uses two buffers");
     static_assert(SPB == 1 || IPL == 1, "split batches need one item per lane");
 };
@@ -509,17 +515,19 @@ __device__ __forceinline__ bool walk_unit(const Problem& p, int i, int j, int cs
 
     const int nb = (__reduce_max_sync(kFull, nitems) + MB - 1) / MB;
     const int nst = nb * SPB;
-    ItemBatch<K> A, B, C;
-    decode(A);
-    decode(B);
-    decode(C);
+    // q[r]: batch b + r, b the batch being summed
+    ItemBatch<K> q[K::DEPTH];
+#pragma unroll
+    for (int r = 0; r < K::DEPTH; ++r) decode(q[r]);
+    ItemBatch<K>& A = q[0];
+    ItemBatch<K>& B = q[1];
     // stage t of the walk lies in batch t / SPB; batch b, b+1, b+2 are A, B, C
     auto issue_lsu_stage = [&](int t, int b) {
         const int bt = t / SPB;
         const int ht = t - bt * SPB;
-        if (bt == b) issue_lsu(t, A, ht);
-        else if (bt == b + 1) issue_lsu(t, B, ht);
-        else issue_lsu(t, C, ht);
+#pragma unroll
+        for (int r = 0; r <= K::REL; ++r)
+            if (bt == b + r) issue_lsu(t, q[r], ht);
     };
     if constexpr (K::TMA) {
         if (nst > 0) issue_tma(0, A, 0);
@@ -556,9 +564,9 @@ __device__ __forceinline__ bool walk_unit(const Problem& p, int i, int j, int cs
             consume_lsu(t, A, h);
         }
         if (h == SPB - 1) {
-            A = B;
-            B = C;
-            decode(C);
+#pragma unroll
+            for (int r = 0; r + 1 < K::DEPTH; ++r) q[r] = q[r + 1];
+            decode(q[K::DEPTH - 1]);
         }
     }
     if (tail_row >= 0) piece_row<K>(p, i, j, gc, tail_row, true, nullptr, lc, tq, gmask, leader);
@@ -566,10 +574,11 @@ __device__ __forceinline__ bool walk_unit(const Problem& p, int i, int j, int cs
     return true;
 }
 
-// Per-warp set-up of the staging region and its mbarriers; returns the
-// warp's staging base and sets bar0.
+// Per-warp set-up of the staging region (stage_bytes per warp) and its
+// mbarriers; returns the warp's staging base and sets bar0.
 template <class K>
-__device__ __forceinline__ uint32_t warp_staging(int lane, uint32_t& bar0) {
+__device__ __forceinline__ uint32_t warp_staging(int lane, uint32_t& bar0,
+                                                 int stage_bytes = K::STAGE_BYTES) {
     const int warps = blockDim.x >> 5;
     const int w = threadIdx.x >> 5;
     const uint32_t smem = (uint32_t)__cvta_generic_to_shared(spmm_dyn_smem);
@@ -582,7 +591,7 @@ __device__ __forceinline__ uint32_t warp_staging(int lane, uint32_t& bar0) {
         }
         __syncwarp();
     }
-    return smem + (uint32_t)(warps * 16 + w * K::STAGE_BYTES);
+    return smem + (uint32_t)(warps * 16 + w * stage_bytes);
 }
 
 // The persistent kernel: each warp is an independent worker.
@@ -595,6 +604,32 @@ spmm_csr_persistent(const Problem p, int flags) {
     const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     uint32_t bar0 = 0, phases = 0;
     const uint32_t wbase = warp_staging<K>(lane, bar0);
+    if (flags & kFlagInterleave) {
+        // ticket k of tile row i is chunk k / TC of tile (i, k % TC); the
+        // tile row's first counter is its queue
+        const int home_i = (flags & kFlagLockstep) ? 0 : (int)blockIdx.x % p.TR;
+        for (int step = 0; step < p.TR; ++step) {
+            int i = home_i + step;
+            if (i >= p.TR) i -= p.TR;
+            const int nsub = p.blk_base[i + 1] - p.blk_base[i];
+            const int total = (nsub + K::G - 1) / K::G * p.TC;
+            int* ctr = p.tile_ctr + i * p.TC;
+            if (total == 0 || ld_relaxed(ctr) >= total) continue;
+            while (true) {
+                int k = 0;
+                if (lane == 0) k = atomicAdd(ctr, 1);
+                k = __shfl_sync(kFull, k, 0);
+                if (k >= total) break;
+                const int c = k / p.TC;
+                const int j = k - c * p.TC;
+                const LaneCols<K::VPL> lc = lane_cols<K, K::VPL, K::LPN>(p, j, lane % K::LPN);
+                const int cs = c * K::G + g;
+                if (!walk_unit<K>(p, i, j, cs < nsub ? cs : -1, lc, lane, wbase, bar0, phases))
+                    return;
+            }
+        }
+        return;
+    }
     const int T = p.TR * p.TC;
     const bool sweep = (flags & kFlagSweep) != 0;
     const int home = (flags & kFlagLockstep) ? 0

@@ -62,7 +62,9 @@ def test_widths(N):
 
 @pytest.mark.parametrize("opts", [dict(warps_per_cta=4), dict(tile_order=1), dict(tile_order=2),
                                   dict(tile_order=4), dict(plan=False),
-                                  dict(warps_per_cta=4, tile_order=5)])
+                                  dict(warps_per_cta=4, tile_order=5), dict(tile_order=8),
+                                  dict(tile_order=9), dict(tile_order=16), dict(tile_order=24),
+                                  dict(warps_per_cta=4, tile_order=16)])
 def test_launch_options(opts):
     A = inputs.rmat_csr(12, 8, seed=6)
     N = 32
@@ -225,7 +227,8 @@ def test_validator():
     assert binding.spmm_get_device_status(ws) == 0
 
 
-def test_every_unit_reserved_exactly_once_under_imbalance():
+@pytest.mark.parametrize("tile_order", [0, 9, 16])
+def test_every_unit_reserved_exactly_once_under_imbalance(tile_order):
     """Work reservation (Section 3.4): with one huge row and many empty ones on a
     16 x 4 grid, the result equals the oracle, so every chunk of every tile was
     processed exactly once (a missed unit leaves NaN, a doubled one doubles)."""
@@ -240,6 +243,6 @@ def test_every_unit_reserved_exactly_once_under_imbalance():
     A = CSR(torch.from_numpy(rowptr.astype(np.int32)), torch.from_numpy(colind.astype(np.int32)),
             torch.ones(colind.size), M, K)
     B = torch.ones(K, N)
-    C, st = run_spmm(A, B, N, tile_rows=16, tile_cols=4, chunk_items=32)
+    C, st = run_spmm(A, B, N, tile_rows=16, tile_cols=4, chunk_items=32, tile_order=tile_order)
     assert st == 0
     assert torch.equal(C[:, 0], torch.from_numpy(lens.astype(np.float32)))
