@@ -208,7 +208,7 @@ def cpu_oracle_sample(A, B, seconds: float):
         stride //= 4
     # a whole pass that is still short is repeated until the time budget is used
     reps = 1
-    while stride == 1 and total_t < seconds / 4:
+    while stride == 1 and total_t < seconds:
         t = time.perf_counter()
         oracle.spmm_rows(rp, ci, v, Bh, rows)
         total_t += time.perf_counter() - t
