@@ -220,6 +220,26 @@ def cpu_oracle_sample(A, B, seconds: float):
     return total_flops / total_t / 1e9, oracle.get_threads(), desc, total_t
 
 
+def job_throughput(local_total_ms: float, steps: int, flops_per_step: float, world: int,
+                   device) -> tuple[float, float]:
+    """Replicas: every rank runs the same product.  The job's step time is the
+    slowest rank's (max over ranks, one all-reduce when world > 1), and its
+    throughput counts the work of all ranks: (ms per step, job GFLOP/s)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([local_total_ms], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_step = float(t.item()) / steps
+    return ms_step, flops_per_step * world / (ms_step * 1e-3) / 1e9
+
+
+def workload_label(args, N: int) -> str:
+    if (args.scale, N, args.grid) == (22, 128, "16x4"):
+        return WORKLOAD
+    return f"rmat-s{args.scale}-ef16-n{N}-fp32-grid{args.grid}"
+
+
 def run_reference(args):
     """The FP64 oracle on the host cores (rank 0 only)."""
     import torch
@@ -242,7 +262,8 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": flops_step / (value * 1e9) * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "M": A.M, "K": A.K, "N": args.n, "nnz": A.nnz},
+        "config": {"workload": workload_label(args, args.n), "M": A.M, "K": A.K, "N": args.n,
+                   "nnz": A.nnz, "tile_grid": args.grid},
         "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
                          "sample": desc},
         "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
@@ -304,13 +325,8 @@ def run_ours(args):
     sampler.stop()
     total_ms = ev[0].elapsed_time(ev[-1])
     per_launch = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_step = total_ms / args.steps
     flops = 2.0 * nnz * N
-    value = flops * world / (ms_step * 1e-3) / 1e9
+    ms_step, value = job_throughput(total_ms, args.steps, flops, world, dev)
 
     # roofline of the dominant kernel (one launch per step)
     peak, peak_kind = measured_peaks()
@@ -383,8 +399,7 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD if (args.scale, N, args.grid) == (22, 128, "16x4")
-                       else f"rmat-s{args.scale}-ef16-n{N}-fp32-grid{args.grid}",
+            "config": {"workload": workload_label(args, N),
                        "M": M, "K": K, "N": N, "nnz": nnz, "tile_grid": args.grid,
                        "chunks": chunks, "work_units": units, "tile_order": args.order,
                        "parallelism": f"replicas x{world}" if world > 1 else "1 gpu",
