@@ -8,9 +8,10 @@
 //   rowind[p]    = row of nonzero perm[p],
 //   vals_t[p]    = vals[perm[p]],
 //   colptr[c]    = first p whose column >= c (binary search of the sorted keys).
-// Each radix pass is three kernels: per-tile digit counts, one exclusive scan
-// over the digit-major count table, and a stable scatter in which every tile
-// ranks its keys in index order (warp match + per-warp digit counts).
+// Each radix pass is per-tile digit counts, an exclusive scan over the
+// digit-major count table (three small kernels), and a stable scatter in which
+// every tile ranks its keys in index order (a warp-level multisplit) and
+// writes each digit's keys as one contiguous run.
 #include "api_internal.cuh"
 
 namespace spmm {
@@ -43,10 +44,16 @@ radix_count_kernel(const int32_t* __restrict__ keys, int64_t n, int shift, int64
     __syncthreads();
     const int64_t tile = blockIdx.x;
     const int64_t base = tile * kTile;
+    int32_t rkey[kSortItems];
+#pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
         const int64_t idx = base + (int64_t)k * kSortThreads + threadIdx.x;
-        if (idx < n) atomicAdd(&h[((uint32_t)keys[idx] >> shift) & 0xff], 1);
+        rkey[k] = idx < n ? keys[idx] : 0;
     }
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k)
+        if (base + (int64_t)k * kSortThreads + threadIdx.x < n)
+            atomicAdd(&h[((uint32_t)rkey[k] >> shift) & 0xff], 1);
     __syncthreads();
     for (int d = threadIdx.x; d < kRadix; d += kSortThreads) counts[(int64_t)d * ntiles + tile] = h[d];
 }
@@ -82,73 +89,137 @@ __global__ void scan_sums_serial_kernel(int64_t* sums, int64_t nb) {
 __global__ void __launch_bounds__(1024)
 scan_apply_kernel(int32_t* __restrict__ data, int64_t n, int64_t per_block,
                   const int64_t* __restrict__ sums) {
-    __shared__ int64_t part[1024];
+    // The block's range, 1024 elements at a time: coalesced loads, a warp
+    // shuffle scan, a scan of the 32 warp totals, and a running block offset.
+    __shared__ int64_t wsum[32];
+    __shared__ int64_t carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t lo = (int64_t)blockIdx.x * per_block;
     const int64_t hi = min(n, lo + per_block);
-    const int64_t chunk = (per_block + blockDim.x - 1) / blockDim.x;
-    const int64_t a = min(hi, lo + (int64_t)threadIdx.x * chunk);
-    const int64_t b = min(hi, a + chunk);
-    int64_t s = 0;
-    for (int64_t i = a; i < b; ++i) s += data[i];
-    part[threadIdx.x] = s;
+    if (threadIdx.x == 0) carry = sums[blockIdx.x];
     __syncthreads();
-    // Hillis-Steele inclusive scan of the 1024 thread sums
-    for (int off = 1; off < 1024; off <<= 1) {
-        const int64_t v = (int)threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+    for (int64_t t0 = lo; t0 < hi; t0 += 1024) {
+        const int64_t i = t0 + threadIdx.x;
+        const int64_t v = i < hi ? data[i] : 0;
+        int64_t x = v;   // inclusive scan within the warp
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int64_t y = __shfl_up_sync(kFull, x, off);
+            if (lane >= off) x += y;
+        }
+        if (lane == 31) wsum[warp] = x;
         __syncthreads();
-        part[threadIdx.x] += v;
+        if (warp == 0) {
+            int64_t w = wsum[lane];
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int64_t y = __shfl_up_sync(kFull, w, off);
+                if (lane >= off) w += y;
+            }
+            wsum[lane] = w;   // inclusive over warps
+        }
         __syncthreads();
-    }
-    int64_t run = sums[blockIdx.x] + (threadIdx.x ? part[threadIdx.x - 1] : 0);
-    for (int64_t i = a; i < b; ++i) {
-        const int32_t v = data[i];
-        data[i] = (int32_t)run;
-        run += v;
+        const int64_t base = carry + (warp ? wsum[warp - 1] : 0);
+        if (i < hi) data[i] = (int32_t)(base + x - v);
+        __syncthreads();
+        if (threadIdx.x == 0) carry += wsum[31];
+        __syncthreads();
     }
 }
 
-// Stable scatter of one radix pass.  Keys of the tile are taken in rounds of
-// kSortThreads consecutive keys; within a round, warp w's keys precede warp
-// w+1's, and lanes are in index order, so ranks follow index order.
+// Stable scatter of one radix pass (a warp-level multisplit).  Warp w owns
+// keys w*KW .. w*KW+KW-1 of the tile (KW = 32 * kSortItems), taken 32 at a
+// time in index order; within each group of 32, the lanes holding the same
+// digit are found with match_any, and each key's rank within its digit is the
+// warp's running count of that digit plus its rank among those lanes.  Keys
+// are then placed in shared memory at (tile-local start of the digit) +
+// (earlier warps' count of the digit) + (rank): (digit, index) order, stable.
+// The tile is written out in that order, so each digit's keys leave as one
+// contiguous run at the digit's global offset (coalesced stores).
 __global__ void __launch_bounds__(kSortThreads)
 radix_scatter_kernel(const int32_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in,
                      int64_t n, int shift, int64_t ntiles, const int32_t* __restrict__ offsets,
                      int32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out) {
     constexpr int W = kSortThreads / 32;
-    __shared__ int32_t base[kRadix];        // running position of each digit in this tile
-    __shared__ int32_t wcnt[W][kRadix];     // per-warp digit counts of the current round
+    constexpr int KW = 32 * kSortItems;     // keys per warp
+    __shared__ int32_t wc[W][kRadix];       // per-warp digit counts, then per-warp offsets
+    __shared__ int32_t tot[kRadix];         // tile digit counts
+    __shared__ int32_t lstart[kRadix];      // tile-local start of each digit
+    __shared__ int32_t gdelta[kRadix];      // global offset - local start, per digit
+    __shared__ int32_t skey[kTile];
+    __shared__ int32_t sval[kTile];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t tile = blockIdx.x;
-    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) base[d] = offsets[(int64_t)d * ntiles + tile];
+    const int64_t t0 = tile * kTile;
+    const int cnt = (int)min((int64_t)kTile, n - t0);
+    for (int q = threadIdx.x; q < W * kRadix; q += kSortThreads) (&wc[0][0])[q] = 0;
+    int32_t rkey[kSortItems], rval[kSortItems];
+#pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
-        for (int q = threadIdx.x; q < W * kRadix; q += kSortThreads) (&wcnt[0][0])[q] = 0;
-        __syncthreads();
-        const int64_t idx = tile * kTile + (int64_t)k * kSortThreads + threadIdx.x;
-        const bool ok = idx < n;
-        const int32_t key = ok ? keys_in[idx] : 0;
-        const int32_t val = ok ? (vals_in ? vals_in[idx] : (int32_t)idx) : 0;
-        const int d = ok ? (int)(((uint32_t)key >> shift) & 0xff) : kRadix;  // kRadix = none
+        const int li = warp * KW + k * 32 + lane;
+        rkey[k] = li < cnt ? keys_in[t0 + li] : 0;
+        rval[k] = li < cnt ? (vals_in ? vals_in[t0 + li] : (int32_t)(t0 + li)) : 0;
+    }
+    __syncthreads();
+    int32_t rr[kSortItems];   // rank within (warp, digit)
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+        const bool ok = warp * KW + k * 32 + lane < cnt;
+        const int d = ok ? (int)(((uint32_t)rkey[k] >> shift) & 0xff) : kRadix;   // kRadix = none
         const unsigned peers = __match_any_sync(kFull, d);
-        const int rank = __popc(peers & ((1u << lane) - 1u));
-        if (ok && rank == 0) wcnt[warp][d] = __popc(peers);
-        __syncthreads();
-        // exclusive prefix over warps for each digit; advance the running base
-        for (int dd = threadIdx.x; dd < kRadix; dd += kSortThreads) {
-            int32_t run = base[dd];
-            for (int w = 0; w < W; ++w) {
-                const int32_t c = wcnt[w][dd];
-                wcnt[w][dd] = run;
-                run += c;
+        const int r = __popc(peers & ((1u << lane) - 1u));
+        const int32_t before = ok ? wc[warp][d] : 0;
+        rr[k] = before + r;
+        __syncwarp();
+        if (ok && r == 0) wc[warp][d] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // per digit: offsets of the warps, and the tile total
+    for (int d = threadIdx.x; d < kRadix; d += kSortThreads) {
+        int32_t run = 0;
+        for (int w = 0; w < W; ++w) {
+            const int32_t c = wc[w][d];
+            wc[w][d] = run;
+            run += c;
+        }
+        tot[d] = run;
+    }
+    __syncthreads();
+    if (warp == 0) {   // exclusive scan of the digit totals
+        int32_t run = 0;
+        for (int d0 = 0; d0 < kRadix; d0 += 32) {
+            const int32_t c = tot[d0 + lane];
+            int32_t x = c;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int32_t y = __shfl_up_sync(kFull, x, off);
+                if (lane >= off) x += y;
             }
-            base[dd] = run;
+            lstart[d0 + lane] = run + x - c;
+            run += __shfl_sync(kFull, x, 31);
         }
-        __syncthreads();
-        if (ok) {
-            const int32_t pos = wcnt[warp][d] + rank;
-            keys_out[pos] = key;
-            vals_out[pos] = val;
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += kSortThreads)
+        gdelta[d] = offsets[(int64_t)d * ntiles + tile] - lstart[d];
+#pragma unroll
+    for (int k = 0; k < kSortItems; ++k) {
+        if (warp * KW + k * 32 + lane < cnt) {
+            const int d = (int)(((uint32_t)rkey[k] >> shift) & 0xff);
+            const int32_t lp = lstart[d] + wc[warp][d] + rr[k];
+            skey[lp] = rkey[k];
+            sval[lp] = rval[k];
         }
-        __syncthreads();
+    }
+    __syncthreads();
+    // write out in (digit, index) order: runs of equal digits are contiguous
+    for (int lp = threadIdx.x; lp < cnt; lp += kSortThreads) {
+        const int32_t key = skey[lp];
+        const int d = (int)(((uint32_t)key >> shift) & 0xff);
+        const int64_t pos = (int64_t)gdelta[d] + lp;
+        keys_out[pos] = key;
+        vals_out[pos] = sval[lp];
     }
 }
 
@@ -192,7 +263,7 @@ static TransposeLayout transpose_layout(int64_t nnz) {
     L.ntiles = (nnz + kTile - 1) / kTile;
     if (L.ntiles < 1) L.ntiles = 1;
     L.ncounts = L.ntiles * kRadix;
-    L.per_block = 64 * kScanBlock;
+    L.per_block = 8 * kScanBlock;
     L.scan_blocks = (L.ncounts + L.per_block - 1) / L.per_block;
     size_t off = 0;
     const size_t a = up256(4 * (size_t)(nnz > 0 ? nnz : 1));
