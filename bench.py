@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--order", type=int, default=16,
                     help="spmm_tuning.tile_order (16: one queue per tile row, chunks of its "
                          "tiles handed out in turn)")
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--context", action="store_true",
@@ -361,11 +361,53 @@ def run_ours(args):
             C_h.copy_(C, non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize()
-        e2e_ms = e0.elapsed_time(e1) / n_e2e
+        serial_ms = e0.elapsed_time(e1) / n_e2e
+        # pipelined: step k+1's inputs copy in (one stream) while step k computes
+        # (the launching stream) and step k-1's result copies out (a third
+        # stream); device inputs and C are double-buffered.  Every step's H2D
+        # and D2H are still inside the timed region.
+        s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+        dbuf = [(rp_d, ci_d, v_d, B_d, C)] + [
+            (torch.empty_like(rp_d), torch.empty_like(ci_d), torch.empty_like(v_d),
+             torch.empty_like(B_d), torch.empty_like(C))]
+        C_hs = [C_h, torch.empty(M, N).pin_memory()]
+        done_in = [torch.cuda.Event() for _ in range(2)]
+        done_comp = [torch.cuda.Event() for _ in range(2)]
+        done_out = [torch.cuda.Event() for _ in range(2)]
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(s_in)
+        for k in range(n_e2e):
+            b = k % 2
+            rp_b, ci_b, v_b, B_b, C_b = dbuf[b]
+            with torch.cuda.stream(s_in):
+                if k >= 2:
+                    s_in.wait_event(done_comp[b])
+                rp_b.copy_(rp_h, non_blocking=True)
+                ci_b.copy_(ci_h, non_blocking=True)
+                v_b.copy_(v_h, non_blocking=True)
+                B_b.copy_(B_h, non_blocking=True)
+                done_in[b].record(s_in)
+            stream.wait_event(done_in[b])
+            if k >= 2:
+                stream.wait_event(done_out[b])
+            binding.spmm_csr(rp_b, ci_b, v_b, B_b, C_b, M, K, N, nnz, plan=plan, ws=ws,
+                             stream=stream)
+            done_comp[b].record(stream)
+            with torch.cuda.stream(s_out):
+                s_out.wait_event(done_comp[b])
+                C_hs[b].copy_(C_b, non_blocking=True)
+                done_out[b].record(s_out)
+        s_out.wait_event(done_comp[(n_e2e - 1) % 2])
+        p1.record(s_out)
+        torch.cuda.synchronize()
+        e2e_ms = p0.elapsed_time(p1) / n_e2e
         e2e = {"value": flops * world / (e2e_ms * 1e-3) / 1e9, "unit": "GFLOP/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
-               "steps": n_e2e}
-        del rp_h, ci_h, v_h, B_h, C_h, B_d
+               "steps": n_e2e, "pipelined": True,
+               "serial_ms_per_step": serial_ms,
+               "serial_value": flops * world / (serial_ms * 1e-3) / 1e9}
+        del rp_h, ci_h, v_h, B_h, C_h, C_hs, B_d, dbuf
 
     # optional context: the paper's own local kernel, cuSPARSE SpMM (through
     # torch.sparse.mm), on the same A and B; not a target and not a backend
