@@ -1,10 +1,11 @@
 // SDDMM at A's pattern: out[e] = sum_n dC[row_e, n] * B[col_e, n].
 //
 // This is the gradient of sum(dC .* (A B)) with respect to A's values.  It uses
-// the SpMM plan with one column block (each group covers the whole row of B),
-// the same per-tile reservation and stealing loop, and the same split between
-// rows walked by one group and rows walked by the whole warp.  Every output is
-// one nonzero, so rows cut by chunk boundaries need no fix-up.
+// the SpMM plan with one column block (a lane group covers the whole row of B),
+// the same per-tile reservation and stealing loop, and the same per-group walk
+// over merge-path sub-chunks, with both the B row and the dC row of every
+// nonzero staged through shared memory by cp.async.  Every output is one
+// nonzero, so rows cut by sub-chunk boundaries need no fix-up.
 #include <string.h>
 
 #include "api_internal.cuh"
@@ -13,31 +14,6 @@
 
 namespace spmm {
 
-// partial dot product of this lane's columns: sum_e d[e] * decode(v)[e]
-template <class Tag>
-__device__ __forceinline__ float dot_vec(const float* d, const uint4& v);
-
-template <>
-__device__ __forceinline__ float dot_vec<TagF32>(const float* d, const uint4& v) {
-    float a = d[0] * __uint_as_float(v.x);
-    float b = d[1] * __uint_as_float(v.y);
-    a = fmaf(d[2], __uint_as_float(v.z), a);
-    b = fmaf(d[3], __uint_as_float(v.w), b);
-    return a + b;
-}
-template <>
-__device__ __forceinline__ float dot_vec<TagBF16>(const float* d, const uint4& v) {
-    float a = d[0] * bf16lo(v.x);
-    float b = d[1] * bf16hi(v.x);
-    a = fmaf(d[2], bf16lo(v.y), a);
-    b = fmaf(d[3], bf16hi(v.y), b);
-    a = fmaf(d[4], bf16lo(v.z), a);
-    b = fmaf(d[5], bf16hi(v.z), b);
-    a = fmaf(d[6], bf16lo(v.w), a);
-    b = fmaf(d[7], bf16hi(v.w), b);
-    return a + b;
-}
-
 struct SddmmProblem {
     Problem p;           // rowptr, colind, B, ldb, M, N, plan arrays, tile_ctr, status
     const float* dC;
@@ -45,130 +21,277 @@ struct SddmmProblem {
     float* out;
 };
 
+// Staging shape of the SDDMM walk: each nonzero item stages its B row
+// segment (VPL vectors per lane) and its dC row segment (VPL*DV float4 per
+// lane), SS items per stage, two stages per warp.
 template <class K>
-__device__ __forceinline__ void load_dc_row(const SddmmProblem& s, int64_t r,
-                                            const LaneCols<K::VPL>& lc, float* d) {
-    const float* src = s.dC + r * s.lddc + lc.c_off;
-#pragma unroll
-    for (int q = 0; q < K::VPL; ++q) {
-#pragma unroll
-        for (int h = 0; h < K::EPV / 4; ++h) {
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if ((lc.vmask >> q) & 1u) v = __ldg(reinterpret_cast<const float4*>(src + q * K::LPN * K::EPV + h * 4));
-            float* o = d + q * K::EPV + h * 4;
-            o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
-        }
-    }
-}
+struct SCfg {
+    static constexpr int DV = K::EPV / 4;                       // dC float4s per B vector
+    static constexpr int SLOTS = K::VPL * (1 + DV);             // 16-byte slots per item per lane
+    static constexpr int SS0 = 8 / SLOTS < 1 ? 1 : 8 / SLOTS;
+    static constexpr int SS = (K::IPL > 1 || SS0 > K::MB) ? K::MB : SS0;
+    static constexpr int SPB = K::MB / SS;
+    static constexpr int STAGE = SS * SLOTS * 32 * 16;           // bytes of one stage buffer
+    static constexpr int STAGE_BYTES = 2 * STAGE;                // per warp
+    static_assert(SPB == 1 || K::IPL == 1, "split batches need one item per lane");
+};
 
-// group-of-LPN sum; lane sl == 0 of the group ends with the total
-template <int LPN>
-__device__ __forceinline__ float group_sum(float x) {
-#pragma unroll
-    for (int off = LPN / 2; off > 0; off >>= 1) x += __shfl_xor_sync(kFull, x, off);
-    return x;
-}
-
+// One group's walk over sub-chunk cs of row block i (cs < 0: none), in the
+// same merge order as the SpMM walk: nonzero items are dotted, row ends only
+// advance the row.  Per stage, lane l of a group holds partial dot products
+// of the stage's items over its own columns; a butterfly across the group
+// (plain halves while the group is wider than the stage, then a transposed
+// exchange) leaves item s's total in the lane that decoded item s, which
+// writes out[e] (consecutive nonzeros, coalesced).
 template <class K, class Tag>
-__device__ __forceinline__ void sddmm_unit(const SddmmProblem& s, int i, int c,
-                                           const LaneCols<K::VPL>& lc, int lane) {
-    const Problem& p = s.p;
-    const int g = lane / K::LPN;
-    const int sl = lane - g * K::LPN;
-    const int gc = p.blk_base[i] + c;
-    const int bi = gc + i;
-    const int x0 = p.bnd_row[bi], y0 = p.bnd_nnz[bi];
-    const int x1 = p.bnd_row[bi + 1], y1 = p.bnd_nnz[bi + 1];
-    const int row_lo = i * p.RB;
-    const int row_hi = min(p.M, row_lo + p.RB);
-    if (x0 > x1 || y0 > y1 || x0 < row_lo || x1 > row_hi) {
-        if (lane == 0) atomicOr(p.status + 1, 1);
-        return;
+__device__ __forceinline__ void sddmm_walk(const SddmmProblem& sp, int i, int cs,
+                                           const LaneCols<K::VPL>& lc, int lane, uint32_t wbase) {
+    using S = SCfg<K>;
+    const Problem& p = sp.p;
+    constexpr int LPN = K::LPN, MB = K::MB, IPL = K::IPL, VPL = K::VPL;
+    constexpr int SS = S::SS, SPB = S::SPB, DV = S::DV, EPV = K::EPV;
+    const int g = lane / LPN;
+    const int tq = lane - g * LPN;
+
+    int x0 = 0, y0 = 0, x1 = 0, y1 = 0;
+    if (cs >= 0) {
+        const int gc = p.blk_base[i] + cs;
+        const int bi = gc + i;
+        x0 = p.bnd_row[bi];
+        y0 = p.bnd_nnz[bi];
+        x1 = p.bnd_row[bi + 1];
+        y1 = p.bnd_nnz[bi + 1];
+        const int row_lo = i * p.RB;
+        const int row_hi = min(p.M, row_lo + p.RB);
+        if (x0 > x1 || y0 > y1 || x0 < row_lo || x1 > row_hi) {
+            if (tq == 0) atomicOr(p.status + 1, 1);
+            x0 = x1 = y0 = y1 = 0;
+        }
     }
-    for (int rb = x0; rb <= x1 && rb < row_hi; rb += 32) {
-        const int r = rb + lane;
-        int st = 0, L = 0;
-        if (r <= x1 && r < row_hi) {
-            const int rstart = __ldg(p.rowptr + r);
-            const int rend = (r < x1) ? __ldg(p.rowptr + r + 1) : y1;
-            st = max(rstart, y0);
-            L = max(0, rend - st);
-        }
-        // rows with more nonzeros than groups: whole warp, groups interleaved
-        unsigned lmask = __ballot_sync(kFull, L > K::G);
-        while (lmask) {
-            const int src = __ffs(lmask) - 1;
-            lmask &= lmask - 1;
-            const int rs = __shfl_sync(kFull, st, src);
-            const int rl = __shfl_sync(kFull, L, src);
-            float d[K::NE];
-            load_dc_row<K>(s, (int64_t)rb + src, lc, d);
-            for (int k = 0; k < rl; k += K::G) {
-                const int e = k + g;
-                float part = 0.0f;
-                if (e < rl) {
-                    const int col = __ldg(p.colind + rs + e);
-                    const char* rp = brow(lc, col);
+    const int nitems = (x1 - x0) + (y1 - y0);
+
+    int pg_cur[IPL], pg_nxt[IPL], pg_nx2[IPL];
+    auto load_page = [&](int q, int* out) {
 #pragma unroll
-                    for (int q = 0; q < K::VPL; ++q)
-                        if ((lc.vmask >> q) & 1u)
-                            part += dot_vec<Tag>(d + q * K::EPV, ld_b16(rp + lc.qoff[q]));
-                }
-                part = group_sum<K::LPN>(part);
-                if (e < rl && sl == 0) s.out[rs + e] = part;
+        for (int u = 0; u < IPL; ++u) {
+            const int o = q * MB + tq + u * LPN;
+            out[u] = (o < x1 - x0) ? (__ldg(p.rowptr + x0 + o + 1) - y0 + o) : INT_MAX;
+        }
+    };
+    load_page(0, pg_cur);
+    load_page(1, pg_nxt);
+    load_page(2, pg_nx2);
+    int pq = 2;
+
+    struct Batch {
+        int col[IPL];
+        int e[IPL];
+        uint32_t ends, nz;
+        int rbase;
+    };
+    int beta = 0, ecur = y0, r = x0;
+    auto decode = [&](Batch& B) {
+        uint32_t m = 0;
+#pragma unroll
+        for (int u = 0; u < IPL; ++u) {
+            const unsigned d0 = (unsigned)(pg_cur[u] - beta);
+            const unsigned d1 = (unsigned)(pg_nxt[u] - beta);
+            if (d0 < (unsigned)MB) m |= 1u << d0;
+            if (d1 < (unsigned)MB) m |= 1u << d1;
+        }
+        m = group_or<K>(m, g);
+        const int left = nitems - beta;
+        const uint32_t valid = left >= MB ? low_bits<MB>() : (left > 0 ? ((1u << left) - 1u) : 0u);
+        m &= valid;
+        const uint32_t nz = valid & ~m;
+#pragma unroll
+        for (int u = 0; u < IPL; ++u) {
+            const int t = tq + u * LPN;
+            int c = 0, idx = 0;
+            if ((nz >> t) & 1u) {
+                idx = ecur + t - __popc(m & ((1u << t) - 1u));
+                c = ld_stream_i32(p.colind + idx);
+            }
+            B.col[u] = c;
+            B.e[u] = idx;
+        }
+        B.ends = m;
+        B.nz = nz;
+        B.rbase = r;
+        r += __popc(m);
+        ecur += __popc(nz);
+        beta += MB;
+        const int last = __shfl_sync(kFull, pg_cur[IPL - 1], LPN - 1, LPN);
+        if (last < beta) {
+#pragma unroll
+            for (int u = 0; u < IPL; ++u) {
+                pg_cur[u] = pg_nxt[u];
+                pg_nxt[u] = pg_nx2[u];
+            }
+            ++pq;
+            load_page(pq, pg_nx2);
+        }
+    };
+
+    // slots of item s in a stage buffer: B vector q at (s*SLOTS + q)*512,
+    // dC float4 k of vector q at (s*SLOTS + VPL + q*DV + k)*512 (+ lane*16)
+    // this lane's columns of a dC row, vector by vector; a vector past N is
+    // pointed at column 0 (its copy is zero-filled, but the address stays valid)
+    int64_t dcoff[VPL];
+#pragma unroll
+    for (int q = 0; q < VPL; ++q)
+        dcoff[q] = ((lc.vmask >> q) & 1u) ? (int64_t)lc.c_off + q * LPN * EPV : 0;
+    auto issue = [&](int t, const Batch& X, int h) {
+        const uint32_t buf = wbase + lane * 16 + (uint32_t)(t & 1) * S::STAGE;
+#pragma unroll
+        for (int s = 0; s < SS; ++s) {
+            int tt, cc;
+            if constexpr (SPB == 1) {
+                tt = s;
+                cc = __shfl_sync(kFull, X.col[s / LPN], s % LPN, LPN);
+            } else {
+                tt = h * SS + s;
+                cc = __shfl_sync(kFull, X.col[0], tt, LPN);
+            }
+            const bool live = (X.nz >> tt) & 1u;
+            const int ok = live ? 16 : 0;
+            const int row = X.rbase + __popc(X.ends & ((1u << tt) - 1u));
+            const char* rp = brow(lc, cc);
+            const float* dr = sp.dC + (int64_t)(live ? row : 0) * sp.lddc;
+#pragma unroll
+            for (int q = 0; q < VPL; ++q) {
+                cp_async16(buf + (uint32_t)((s * S::SLOTS + q) * 512), rp + lc.qoff[q], ok);
+#pragma unroll
+                for (int k = 0; k < DV; ++k)
+                    cp_async16(buf + (uint32_t)((s * S::SLOTS + VPL + q * DV + k) * 512),
+                               dr + dcoff[q] + k * 4, ((lc.vmask >> q) & 1u) ? ok : 0);
             }
         }
-        // short rows: one row per group
-        const unsigned smask = __ballot_sync(kFull, L > 0 && L <= K::G);
-        const int nshort = __popc(smask);
-        for (int q0 = 0; q0 < nshort; q0 += K::G) {
-            const int q = q0 + g;
-            const bool act = q < nshort;
-            const int pos = act ? nth_set_bit(smask, q) : 0;
-            const int rs = __shfl_sync(kFull, st, pos);
-            int rl = __shfl_sync(kFull, L, pos);
-            if (!act) rl = 0;
-            float d[K::NE];
-            load_dc_row<K>(s, act ? (int64_t)rb + pos : (int64_t)rb, lc, d);
-            const int tmax = __reduce_max_sync(kFull, rl);
-            for (int e = 0; e < tmax; ++e) {
-                float part = 0.0f;
-                if (e < rl) {
-                    const int col = __ldg(p.colind + rs + e);
-                    const char* rp = brow(lc, col);
+        cp_async_commit();
+    };
+
+    // per-lane partial dot product of item s of the stage
+    auto partial = [&](uint32_t buf, int s) -> float {
+        float a = 0.0f, b = 0.0f;
 #pragma unroll
-                    for (int qq = 0; qq < K::VPL; ++qq)
-                        if ((lc.vmask >> qq) & 1u)
-                            part += dot_vec<Tag>(d + qq * K::EPV, ld_b16(rp + lc.qoff[qq]));
-                }
-                part = group_sum<K::LPN>(part);
-                if (e < rl && sl == 0) s.out[rs + e] = part;
+        for (int q = 0; q < VPL; ++q) {
+            const uint4 bv = lds128(buf + (uint32_t)((s * S::SLOTS + q) * 512));
+            float bf[EPV];
+            if constexpr (EPV == 4) {
+                bf[0] = __uint_as_float(bv.x); bf[1] = __uint_as_float(bv.y);
+                bf[2] = __uint_as_float(bv.z); bf[3] = __uint_as_float(bv.w);
+            } else {
+                const uint32_t w[4] = {bv.x, bv.y, bv.z, bv.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) { bf[2 * k] = bf16lo(w[k]); bf[2 * k + 1] = bf16hi(w[k]); }
             }
+#pragma unroll
+            for (int k = 0; k < DV; ++k) {
+                const uint4 dv = lds128(buf + (uint32_t)((s * S::SLOTS + VPL + q * DV + k) * 512));
+                a = fmaf(__uint_as_float(dv.x), bf[4 * k + 0], a);
+                b = fmaf(__uint_as_float(dv.y), bf[4 * k + 1], b);
+                a = fmaf(__uint_as_float(dv.z), bf[4 * k + 2], a);
+                b = fmaf(__uint_as_float(dv.w), bf[4 * k + 3], b);
+            }
+        }
+        return a + b;
+    };
+
+    auto consume = [&](int t, const Batch& X, int h) {
+        const uint32_t buf = wbase + lane * 16 + (uint32_t)(t & 1) * S::STAGE;
+        float v[SS];
+#pragma unroll
+        for (int s = 0; s < SS; ++s) v[s] = partial(buf, s);
+        if constexpr (SS <= LPN) {
+            // plain halves while the group is wider than the stage ...
+#pragma unroll
+            for (int off = LPN / 2; off >= SS; off >>= 1)
+#pragma unroll
+                for (int s = 0; s < SS; ++s) v[s] += __shfl_xor_sync(kFull, v[s], off);
+            // ... then a transposed exchange: lane l keeps item l % SS
+#pragma unroll
+            for (int off = SS / 2, cnt = SS; off >= 1; off >>= 1, cnt >>= 1) {
+                const bool up = (tq & off) != 0;
+#pragma unroll
+                for (int j = 0; j < cnt / 2; ++j) {
+                    const float send = up ? v[j] : v[j + cnt / 2];
+                    const float keep = up ? v[j + cnt / 2] : v[j];
+                    v[j] = keep + __shfl_xor_sync(kFull, send, off);
+                }
+            }
+            // lane h*SS + s decoded item h*SS + s and now holds its total
+            const int tt = (SPB == 1 ? 0 : h * SS) + (tq % SS);
+            if ((tq / SS) == (SPB == 1 ? 0 : h) && ((X.nz >> tt) & 1u)) sp.out[X.e[0]] = v[0];
+        } else {
+            // a stage wider than the group (lanes hold several items): sum
+            // each item over the group; the lane that decoded it writes it
+#pragma unroll
+            for (int off = LPN / 2; off >= 1; off >>= 1)
+#pragma unroll
+                for (int s = 0; s < SS; ++s) v[s] += __shfl_xor_sync(kFull, v[s], off);
+#pragma unroll
+            for (int s = 0; s < SS; ++s)
+                if ((s % LPN) == tq && ((X.nz >> s) & 1u)) sp.out[X.e[s / LPN]] = v[s];
+        }
+    };
+
+    const int nb = (__reduce_max_sync(kFull, nitems) + MB - 1) / MB;
+    const int nst = nb * SPB;
+    Batch A, B, C;
+    decode(A);
+    decode(B);
+    decode(C);
+    if (nst > 0) issue(0, A, 0);
+#pragma unroll 1
+    for (int t = 0; t < nst; ++t) {
+        const int h = SPB == 1 ? 0 : (t & (SPB - 1));
+        if (t + 1 < nst) {
+            if (SPB > 1 && h + 1 < SPB) issue(t + 1, A, h + 1);
+            else issue(t + 1, B, 0);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        consume(t, A, h);
+        if (h == SPB - 1) {
+            A = B;
+            B = C;
+            decode(C);
         }
     }
 }
+
+#ifndef SPMM_SDDMM_MINBLOCKS
+#define SPMM_SDDMM_MINBLOCKS 3   // resident 256-thread CTAs per SM the register budget targets
+#endif
 
 template <class Tag, int LPN, int VPL>
-__global__ void __launch_bounds__(256, 2) sddmm_persistent(const SddmmProblem s) {
+__global__ void __launch_bounds__(256, SPMM_SDDMM_MINBLOCKS) sddmm_persistent(const SddmmProblem s) {
     using K = KCfg<TagF32, Tag, LPN, VPL>;
+    using SC = SCfg<K>;
     const Problem& p = s.p;
     const int lane = threadIdx.x & 31;
+    const int g = lane / K::LPN;
     const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const uint32_t wbase = (uint32_t)__cvta_generic_to_shared(spmm_dyn_smem) +
+                           (uint32_t)((threadIdx.x >> 5) * SC::STAGE_BYTES);
     const int T = p.TR;
     const int home = warp % T;
     const LaneCols<K::VPL> lc = lane_cols<K, K::VPL, K::LPN>(p, 0, lane % K::LPN);
     for (int step = 0; step < T; ++step) {
         int i = home + step;
         if (i >= T) i -= T;
-        const int nch = p.blk_base[i + 1] - p.blk_base[i];
-        if (nch == 0) continue;
-        if (ld_relaxed(p.tile_ctr + i) >= nch) continue;
+        const int nsub = p.blk_base[i + 1] - p.blk_base[i];
+        const int nun = (nsub + K::G - 1) / K::G;   // units: G sub-chunks each
+        if (nun == 0) continue;
+        if (ld_relaxed(p.tile_ctr + i) >= nun) continue;
         while (true) {
             int c = 0;
             if (lane == 0) c = atomicAdd(p.tile_ctr + i, 1);
             c = __shfl_sync(kFull, c, 0);
-            if (c >= nch) break;
-            sddmm_unit<K, Tag>(s, i, c, lc, lane);
+            if (c >= nun) break;
+            const int cs = c * K::G + g;
+            sddmm_walk<K, Tag>(s, i, cs < nsub ? cs : -1, lc, lane, wbase);
         }
     }
 }
@@ -177,16 +300,21 @@ int device_sm_count();
 
 template <class Tag, int LPN, int VPL>
 static cudaError_t launch_sddmm_one(const SddmmProblem& s, int64_t units, cudaStream_t st) {
+    using K = KCfg<TagF32, Tag, LPN, VPL>;
     auto kern = sddmm_persistent<Tag, LPN, VPL>;
+    const size_t smem = (size_t)8 * SCfg<K>::STAGE_BYTES;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)device_sm_count() * per_sm;
-    const int64_t need = (units + 7) / 8;
+    const int64_t need = ((units + K::G - 1) / K::G + 7) / 8;
     if (grid > need) grid = need;
     if (grid < 1) grid = 1;
-    kern<<<(unsigned)grid, 256, 0, st>>>(s);
+    kern<<<(unsigned)grid, 256, smem, st>>>(s);
     return cudaGetLastError();
 }
 
@@ -241,7 +369,7 @@ extern "C" int spmm_sddmm_csr(const int32_t* A_rowptr, const int32_t* A_colind, 
     } else {
         TR = 1; TC = 1;
         RB = (int32_t)M;
-        D = plan_default_chunk(M, nnz, 1, device_sm_count(), 1);
+        D = plan_default_chunk(M, nnz, 1, device_sm_count(), plan_default_groups(N, 1));
         cap = plan_chunk_cap(M, nnz, TR, D);
         // layout [status, counter (256 B)][plan arrays]
         const size_t pb = plan_array_bytes(TR, cap);
