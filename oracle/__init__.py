@@ -68,6 +68,8 @@ def _load():
             lib.oracle_quantize_rows_e4m3.argtypes = [vp, i64, i64, i64, vp, i64, vp]
             lib.oracle_quantize_rows_e4m3.restype = None
             lib.oracle_set_threads.argtypes = [ci]
+            lib.oracle_spgemm.argtypes = [i64, i64, i64, i32p, i32p, dp, i32p, i32p, dp, i32p,
+                                          vp, vp]
             lib.oracle_set_threads.restype = None
             lib.oracle_get_threads.restype = ci
             _lib = lib
@@ -238,3 +240,26 @@ def abs_bound(rowptr, colind, vals, B) -> np.ndarray:
     v, _ = _float_arr(vals)
     b, _ = _float_arr(B)
     return spmm(rowptr, colind, np.abs(v.astype(np.float64)), np.abs(b.astype(np.float64)))
+
+
+def spgemm(A_rowptr, A_colind, A_vals, B_rowptr, B_colind, B_vals, K: int, N: int):
+    """C = A*B for CSR A (M x K) and CSR B (K x N): (rowptr, colind, vals) in FP64,
+    columns of each row increasing; an entry exists wherever some product
+    A_ik B_kj is formed (explicit zeros count)."""
+    lib = _load()
+    arp, aci = _np(A_rowptr, np.int32), _np(A_colind, np.int32)
+    brp, bci = _np(B_rowptr, np.int32), _np(B_colind, np.int32)
+    av, bv = _np(A_vals, np.float64), _np(B_vals, np.float64)
+    M = arp.size - 1
+    rowptr = np.empty(M + 1, dtype=np.int32)
+    rc = lib.oracle_spgemm(M, K, N, _p(arp), _p(aci), _p(av), _p(brp), _p(bci), _p(bv),
+                           _p(rowptr), None, None)
+    if rc != 0:
+        raise ValueError("column index out of range")
+    nnz = int(rowptr[-1])
+    colind = np.empty(max(nnz, 1), dtype=np.int32)
+    vals = np.empty(max(nnz, 1), dtype=np.float64)
+    rc = lib.oracle_spgemm(M, K, N, _p(arp), _p(aci), _p(av), _p(brp), _p(bci), _p(bv),
+                           _p(rowptr), _p(colind), _p(vals))
+    assert rc == 0
+    return rowptr, colind[:nnz], vals[:nnz]

@@ -22,6 +22,11 @@
  *                            E4M3 saturates to +-448.
  *   oracle_quantize_rows     per-row scaled E4M3: s = amax(row)/448 in FP32
  *                            (s = 1 for an all-zero row), q = E4M3(x / s).
+ *   oracle_spgemm            the sparse-sparse local product C = A*B (the local
+ *                            SpGEMM of Section 5's SpGEMM experiments): row i of
+ *                            C holds column j when some k has A_ik and B_kj
+ *                            stored (explicit zeros count), valued in FP64 as
+ *                            sum_k A_ik B_kj; columns of each row increasing.
  *
  * The paper (Section 4) bounds the local product by the bytes of A, B and C;
  * the oracle makes no attempt at speed beyond an OpenMP loop over rows, which
@@ -293,4 +298,70 @@ void oracle_quantize_rows_e4m3(const float* X, int64_t rows, int64_t cols, int64
             Q[r * ldq + c] = e4m3_encode_one(q);
         }
     }
+}
+
+
+/*
+ * Local SpGEMM, C = A*B with A (M x K) and B (K x N) in CSR: a sparse
+ * accumulator per row (a dense FP64 row of length N with a marker of the row
+ * that last touched each column).  Call with C_colind == NULL to count: it
+ * writes C_rowptr[M+1] only.  Then call again with C_colind and C_vals of
+ * C_rowptr[M] entries to fill them.  Values are summed in FP64 over A's row in
+ * CSR order and, within each term, over B's row in CSR order.
+ */
+static int cmp_i32(const void* a, const void* b) {
+    const int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
+    return (x > y) - (x < y);
+}
+
+int oracle_spgemm(int64_t M, int64_t K, int64_t N, const int32_t* A_rowptr,
+                  const int32_t* A_colind, const double* A_vals, const int32_t* B_rowptr,
+                  const int32_t* B_colind, const double* B_vals, int32_t* C_rowptr,
+                  int32_t* C_colind, double* C_vals) {
+    int64_t* mark = (int64_t*)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+    double* acc = (double*)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+    int32_t* cols = (int32_t*)malloc(sizeof(int32_t) * (size_t)(N > 0 ? N : 1));
+    if (!mark || !acc || !cols) {
+        free(mark); free(acc); free(cols);
+        return ORACLE_ERR;
+    }
+    for (int64_t j = 0; j < N; ++j) mark[j] = -1;
+    int64_t out = 0;
+    if (!C_colind) C_rowptr[0] = 0;
+    for (int64_t i = 0; i < M; ++i) {
+        int64_t n = 0;
+        for (int32_t e = A_rowptr[i]; e < A_rowptr[i + 1]; ++e) {
+            const int32_t k = A_colind[e];
+            if (k < 0 || k >= K) {
+                free(mark); free(acc); free(cols);
+                return ORACLE_ERR;
+            }
+            const double a = A_vals ? A_vals[e] : 1.0;
+            for (int32_t f = B_rowptr[k]; f < B_rowptr[k + 1]; ++f) {
+                const int32_t j = B_colind[f];
+                if (j < 0 || j >= N) {
+                    free(mark); free(acc); free(cols);
+                    return ORACLE_ERR;
+                }
+                if (mark[j] != i) {
+                    mark[j] = i;
+                    acc[j] = 0.0;
+                    cols[n++] = j;
+                }
+                acc[j] += a * (B_vals ? B_vals[f] : 1.0);
+            }
+        }
+        if (!C_colind) {
+            C_rowptr[i + 1] = (int32_t)(C_rowptr[i] + n);
+            continue;
+        }
+        qsort(cols, (size_t)n, sizeof(int32_t), cmp_i32);
+        for (int64_t q = 0; q < n; ++q) {
+            C_colind[out + q] = cols[q];
+            if (C_vals) C_vals[out + q] = acc[cols[q]];
+        }
+        out += n;
+    }
+    free(mark); free(acc); free(cols);
+    return ORACLE_OK;
 }

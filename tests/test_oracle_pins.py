@@ -305,3 +305,98 @@ def test_quantize_rows_e4m3():
             continue
         j = int(np.argmax(np.abs(X[r])))
         assert q[r, j] & 0x7F == 0x7E
+
+
+# ---------------------------------------------------------------- SpGEMM ----
+
+def _rand_csr(rng, M, K, density, dup=False):
+    rows, cols = [], []
+    for i in range(M):
+        cs = np.flatnonzero(rng.random(K) < density)
+        if dup and cs.size:
+            cs = np.sort(np.concatenate([cs, rng.choice(cs, 1)]))
+        rows.append(np.full(cs.size, i))
+        cols.append(cs)
+    rp = np.zeros(M + 1, np.int64)
+    rp[1:] = np.cumsum([c.size for c in cols])
+    ci = np.concatenate(cols).astype(np.int32) if rp[-1] else np.zeros(0, np.int32)
+    v = rng.standard_normal(ci.size)
+    return rp.astype(np.int32), ci, v
+
+
+def _dense(rp, ci, v, K):
+    M = rp.size - 1
+    D = np.zeros((M, K))
+    S = np.zeros((M, K), bool)
+    for i in range(M):
+        for e in range(rp[i], rp[i + 1]):
+            D[i, ci[e]] += v[e]
+            S[i, ci[e]] = True
+    return D, S
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_spgemm_equals_dense_product_on_small_matrices(seed):
+    rng = np.random.default_rng(seed)
+    M, K, N = 9, 7, 11
+    a = _rand_csr(rng, M, K, 0.3, dup=seed % 2 == 1)
+    b = _rand_csr(rng, K, N, 0.35)
+    rp, ci, v = oracle.spgemm(*a, *b, K, N)
+    Ad, As = _dense(*a, K)
+    Bd, Bs = _dense(*b, N)
+    # structure: where some stored A_ik meets some stored B_kj (boolean product)
+    S = (As.astype(int) @ Bs.astype(int)) > 0
+    Cd = np.zeros((M, N))
+    Cs = np.zeros((M, N), bool)
+    for i in range(M):
+        cols = ci[rp[i]:rp[i + 1]]
+        assert np.all(np.diff(cols) > 0)            # increasing, no duplicates
+        Cd[i, cols] = v[rp[i]:rp[i + 1]]
+        Cs[i, cols] = True
+    assert np.array_equal(Cs, S)
+    np.testing.assert_allclose(Cd, Ad @ Bd, rtol=1e-12, atol=1e-12)
+
+
+def test_spgemm_identity_and_permutation_and_diagonal_are_exact():
+    rng = np.random.default_rng(7)
+    K, N = 8, 10
+    b = _rand_csr(rng, K, N, 0.4)
+    eye = (np.arange(K + 1, dtype=np.int32), np.arange(K, dtype=np.int32), np.ones(K))
+    rp, ci, v = oracle.spgemm(*eye, *b, K, N)
+    assert np.array_equal(rp, b[0]) and np.array_equal(ci, b[1]) and np.array_equal(v, b[2])
+    perm = rng.permutation(K)
+    P = (np.arange(K + 1, dtype=np.int32), perm.astype(np.int32), np.ones(K))
+    rp, ci, v = oracle.spgemm(*P, *b, K, N)
+    for i in range(K):
+        k = perm[i]
+        assert np.array_equal(ci[rp[i]:rp[i + 1]], b[1][b[0][k]:b[0][k + 1]])
+        assert np.array_equal(v[rp[i]:rp[i + 1]], b[2][b[0][k]:b[0][k + 1]])
+    d = rng.standard_normal(K)
+    Dg = (np.arange(K + 1, dtype=np.int32), np.arange(K, dtype=np.int32), d)
+    rp, ci, v = oracle.spgemm(*Dg, *b, K, N)
+    for i in range(K):
+        assert np.array_equal(v[rp[i]:rp[i + 1]], d[i] * b[2][b[0][i]:b[0][i + 1]])
+
+
+def test_spgemm_keeps_explicit_zeros_and_empty_rows():
+    # A = [[0 (stored), 0], [none]] times B = [[1, 2]]: row 0 gets both columns, valued 0
+    a = (np.array([0, 1, 1], np.int32), np.array([0], np.int32), np.array([0.0]))
+    b = (np.array([0, 2], np.int32), np.array([0, 1], np.int32), np.array([1.0, 2.0]))
+    rp, ci, v = oracle.spgemm(*a, *b, 1, 2)
+    assert rp.tolist() == [0, 2, 2] and ci.tolist() == [0, 1] and v.tolist() == [0.0, 0.0]
+    empty = (np.zeros(4, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    rp, ci, v = oracle.spgemm(*empty, *b, 1, 2)
+    assert rp.tolist() == [0, 0, 0, 0] and ci.size == 0
+
+
+def test_spgemm_is_associative_with_the_spmm_oracle():
+    # (A B) x == A (B x), the right side through the independent SpMM oracle
+    rng = np.random.default_rng(11)
+    M, K, N = 30, 25, 20
+    a = _rand_csr(rng, M, K, 0.15)
+    b = _rand_csr(rng, K, N, 0.2)
+    x = rng.standard_normal((N, 3))
+    rp, ci, v = oracle.spgemm(*a, *b, K, N)
+    left = oracle.spmm(rp, ci, v, x)
+    right = oracle.spmm(a[0], a[1], a[2], oracle.spmm(b[0], b[1], b[2], x))
+    np.testing.assert_allclose(left, right, rtol=1e-10, atol=1e-10)
