@@ -58,7 +58,10 @@ def parse():
     ap.add_argument("--context", action="store_true",
                     help="also time torch.sparse.mm (cuSPARSE) on the same product, as context")
     ap.add_argument("--batch-count", type=int, default=512)
-    ap.add_argument("--workload", default="rmat", choices=["rmat", "precision", "gcn", "batch"],
+    ap.add_argument("--spgemm-scale", type=int, default=14,
+                    help="R-MAT scale of the A*A SpGEMM workload")
+    ap.add_argument("--workload", default="rmat",
+                    choices=["rmat", "precision", "gcn", "batch", "spgemm"],
                     help="rmat: the benchmark line; the others report the precision, "
                          "backward and batched forms")
     return ap.parse_args()
@@ -635,8 +638,59 @@ def run_batch(args):
     batch.close()
 
 
+def run_spgemm(args):
+    """Local SpGEMM C = A*A on an R-MAT matrix (edge factor 16, FP32 values):
+    the expand-sort-compress product through spmm_spgemm, timed with CUDA events
+    after warm-up, checked against the FP64 oracle on sampled rows."""
+    import ctypes
+    import numpy as np
+    import torch
+    import oracle
+    from paper_2311_18141_gb300 import binding, inputs
+    dev = torch.device("cuda")
+    lib = binding.load_library()
+    A = inputs.rmat_csr(args.spgemm_scale, 16, 0.57, 0.19, 0.19, seed=1, device=dev, values="pos")
+    M, nnz = A.M, A.nnz
+    stream = torch.cuda.current_stream()
+    P, wsb = ctypes.c_int64(), ctypes.c_size_t()
+    assert lib.spmm_spgemm_analyze(A.rowptr.data_ptr(), A.colind.data_ptr(), M, M, nnz,
+                                   A.rowptr.data_ptr(), M, ctypes.byref(P), ctypes.byref(wsb),
+                                   ctypes.c_void_p(stream.cuda_stream)) == 0
+    ws = binding.workspace(wsb.value, dev)
+    E = ctypes.c_int64()
+
+    def step():
+        rc = lib.spmm_spgemm(A.rowptr.data_ptr(), A.colind.data_ptr(), A.vals.data_ptr(), M, M,
+                             nnz, A.rowptr.data_ptr(), A.colind.data_ptr(), A.vals.data_ptr(), M,
+                             P.value, ws.data_ptr(), wsb.value, ctypes.byref(E),
+                             ctypes.c_void_p(stream.cuda_stream))
+        assert rc == 0
+    ms = _time_ms(step, args.steps, args.warmup, stream)
+    rp, ci, v, _ = binding.spgemm(A.rowptr, A.colind, A.vals, M, M, A.rowptr, A.colind, A.vals,
+                                  M, ws=ws)
+    # sampled rows against the oracle
+    rph, cih = A.rowptr.cpu().numpy(), A.colind.cpu().numpy()
+    vh = A.vals.cpu().numpy().astype(np.float64)
+    erp, eci, ev = oracle.spgemm(rph, cih, vh, rph, cih, vh, M, M)
+    got_rp = rp.cpu().numpy()
+    structure_ok = bool(np.array_equal(got_rp, erp) and np.array_equal(ci.cpu().numpy(), eci))
+    _, _, bound = oracle.spgemm(rph, cih, np.abs(vh), rph, cih, np.abs(vh), M, M)
+    rel = np.abs(v.cpu().numpy().astype(np.float64) - ev) / np.maximum(bound, 1e-30)
+    bytes_min = 4 * (M + 1) + 8 * nnz + 4 * (M + 1) + 8 * E.value   # A once, C once
+    print(json.dumps({"workload": f"spgemm-rmat-s{args.spgemm_scale}-AxA", "nnz": nnz,
+                      "products": P.value, "entries": E.value, "ms": ms,
+                      "gflops": 2.0 * P.value / (ms * 1e-3) / 1e9,
+                      "products_per_s": P.value / (ms * 1e-3),
+                      "structure_matches_oracle": structure_ok,
+                      "err_max": float(rel.max()) if rel.size else 0.0,
+                      "min_bytes": bytes_min}), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "spgemm":
+        run_spgemm(args)
+        return
     if args.workload == "precision":
         run_precision(args)
         return

@@ -260,6 +260,40 @@ int spmm_csr_noalloc(const int32_t* A_rowptr, const int32_t* A_colind, const voi
 int spmm_csr_validate(const int32_t* A_rowptr, const int32_t* A_colind, int64_t M, int64_t K,
                       int64_t nnz, void* workspace, size_t workspace_bytes, void* stream);
 
+/*
+ * Local SpGEMM, C = A * B: the sparse-sparse local product of the paper's
+ *   SpGEMM experiments (Section 5), here for CSR A (M x K), CSR B (K x N) and
+ *   CSR C with FP32 values.  Row i of C holds column j wherever some product
+ *   A_ik * B_kj is formed (explicit zeros count), columns increasing; each
+ *   value is the FP32 sum of its products taken in A's CSR order, then B's,
+ *   so results are reproducible.  Three calls:
+ *
+ * spmm_spgemm_analyze -- number of products (sum over A's nonzeros of the
+ *   length of B's row) and the workspace bytes spmm_spgemm needs.  Allocates
+ *   and frees temporary device memory and synchronises `stream`.  Errors:
+ *   SPMM_ERR_INVALID_ARG, SPMM_ERR_BAD_CSR (a column of A outside [0, K)),
+ *   SPMM_ERR_UNSUPPORTED (2^31 - 1 products or more), SPMM_ERR_CUDA.
+ */
+int spmm_spgemm_analyze(const int32_t* A_rowptr, const int32_t* A_colind, int64_t M, int64_t K,
+                        int64_t nnzA, const int32_t* B_rowptr, int64_t N, int64_t* products,
+                        size_t* workspace_bytes, void* stream);
+
+/* spmm_spgemm -- the product into `workspace` (256-byte aligned, at least the
+ * analyzed size; no allocation); *entries := nnz of C.  Synchronises
+ * `stream`.  Errors: SPMM_ERR_INVALID_ARG, SPMM_ERR_WORKSPACE, SPMM_ERR_BAD_CSR
+ * (a column of B outside [0, N)), SPMM_ERR_CUDA. */
+int spmm_spgemm(const int32_t* A_rowptr, const int32_t* A_colind, const float* A_vals, int64_t M,
+                int64_t K, int64_t nnzA, const int32_t* B_rowptr, const int32_t* B_colind,
+                const float* B_vals, int64_t N, int64_t products, void* workspace,
+                size_t workspace_bytes, int64_t* entries, void* stream);
+
+/* spmm_spgemm_copy -- C from the workspace of the spmm_spgemm call with the
+ * same (M, nnzA, products) into caller buffers: C_rowptr[M+1], C_colind and
+ * C_vals of `entries` elements (device).  Enqueued on `stream`. */
+int spmm_spgemm_copy(const void* workspace, int64_t M, int64_t nnzA, int64_t products,
+                     int64_t entries, int32_t* C_rowptr, int32_t* C_colind, float* C_vals,
+                     void* stream);
+
 /* Synchronise `stream`, then copy the device status word of `workspace` into
  * *status (host) and clear it. */
 int spmm_get_device_status(void* workspace, int32_t* status, void* stream);

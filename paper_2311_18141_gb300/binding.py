@@ -37,7 +37,8 @@ EXPORTED = [
     "spmm_csr_transpose", "spmm_gather_values", "spmm_sddmm_csr", "spmm_quantize_rows",
     "spmm_csr_noalloc", "spmm_batch_create", "spmm_batch_destroy", "spmm_batch_workspace_size",
     "spmm_batch_set_shapes", "spmm_batch_get_shapes", "spmm_csr_batched",
-    "spmm_batch_graph_launch", "spmm_batch_autotune",
+    "spmm_batch_graph_launch", "spmm_batch_autotune", "spmm_spgemm_analyze", "spmm_spgemm",
+    "spmm_spgemm_copy",
 ]
 
 
@@ -87,6 +88,11 @@ def load_library(path: str | None = None):
         lib.spmm_plan_destroy.argtypes = [vp]
         lib.spmm_plan_workspace_size.argtypes = [vp, ctypes.POINTER(sz)]
         lib.spmm_plan_units.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        lib.spmm_spgemm_analyze.argtypes = [vp, vp, i64, i64, i64, vp, i64, ctypes.POINTER(i64),
+                                            ctypes.POINTER(sz), vp]
+        lib.spmm_spgemm.argtypes = [vp, vp, vp, i64, i64, i64, vp, vp, vp, i64, i64, vp, sz,
+                                    ctypes.POINTER(i64), vp]
+        lib.spmm_spgemm_copy.argtypes = [vp, i64, i64, i64, i64, vp, vp, vp, vp]
         lib.spmm_csr_workspace_size.argtypes = [i64, i64, i64, i32, i32,
                                                 ctypes.POINTER(spmm_tuning), ctypes.POINTER(sz)]
         lib.spmm_csr.argtypes = [vp, vp, vp, i32, vp, vp, i32, vp, i64, vp, i64, i64, i64, i64,
@@ -370,3 +376,29 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def spgemm(A_rowptr, A_colind, A_vals, M: int, K: int, B_rowptr, B_colind, B_vals, N: int,
+           stream=None, ws: torch.Tensor | None = None):
+    """C = A * B for device CSR A (M x K) and B (K x N), FP32 values: spmm_spgemm_analyze,
+    spmm_spgemm and spmm_spgemm_copy.  Returns (rowptr, colind, vals) on the device."""
+    lib = load_library()
+    nnzA = int(A_colind.numel())
+    P, wsb = ctypes.c_int64(), ctypes.c_size_t()
+    st = _stream(stream)
+    _check(lib.spmm_spgemm_analyze(_ptr(A_rowptr), _ptr(A_colind), int(M), int(K), nnzA,
+                                   _ptr(B_rowptr), int(N), ctypes.byref(P), ctypes.byref(wsb),
+                                   st), "spmm_spgemm_analyze")
+    dev = A_rowptr.device
+    if ws is None or ws.numel() < wsb.value:
+        ws = workspace(wsb.value, dev)
+    E = ctypes.c_int64()
+    _check(lib.spmm_spgemm(_ptr(A_rowptr), _ptr(A_colind), _ptr(A_vals), int(M), int(K), nnzA,
+                           _ptr(B_rowptr), _ptr(B_colind), _ptr(B_vals), int(N), P.value,
+                           _ptr(ws), wsb.value, ctypes.byref(E), st), "spmm_spgemm")
+    rowptr = torch.empty(int(M) + 1, dtype=torch.int32, device=dev)
+    colind = torch.empty(max(E.value, 1), dtype=torch.int32, device=dev)
+    vals = torch.empty(max(E.value, 1), dtype=torch.float32, device=dev)
+    _check(lib.spmm_spgemm_copy(_ptr(ws), int(M), nnzA, P.value, E.value, _ptr(rowptr),
+                                _ptr(colind), _ptr(vals), st), "spmm_spgemm_copy")
+    return rowptr, colind[:E.value], vals[:E.value], P.value

@@ -13,6 +13,7 @@
 // every tile ranks its keys in index order (a warp-level multisplit) and
 // writes each digit's keys as one contiguous run.
 #include "api_internal.cuh"
+#include "radix.cuh"
 
 namespace spmm {
 
@@ -251,32 +252,7 @@ __global__ void finish_kernel(const int32_t* __restrict__ perm, const int32_t* _
     }
 }
 
-struct TransposeLayout {
-    size_t row_of, keys0, keys1, vals0, vals1, counts, sums, total;
-    int64_t ntiles, ncounts, scan_blocks, per_block;
-};
-
 static size_t up256(size_t x) { return (x + 255) / 256 * 256; }
-
-static TransposeLayout transpose_layout(int64_t nnz) {
-    TransposeLayout L;
-    L.ntiles = (nnz + kTile - 1) / kTile;
-    if (L.ntiles < 1) L.ntiles = 1;
-    L.ncounts = L.ntiles * kRadix;
-    L.per_block = 8 * kScanBlock;
-    L.scan_blocks = (L.ncounts + L.per_block - 1) / L.per_block;
-    size_t off = 0;
-    const size_t a = up256(4 * (size_t)(nnz > 0 ? nnz : 1));
-    L.row_of = off; off += a;
-    L.keys0 = off; off += a;
-    L.keys1 = off; off += a;
-    L.vals0 = off; off += a;
-    L.vals1 = off; off += a;
-    L.counts = off; off += up256(4 * (size_t)L.ncounts);
-    L.sums = off; off += up256(8 * (size_t)L.scan_blocks);
-    L.total = off;
-    return L;
-}
 
 static unsigned grid_cap(int64_t work, int threads) {
     int64_t g = (work + threads - 1) / threads;
@@ -284,6 +260,103 @@ static unsigned grid_cap(int64_t work, int threads) {
     if (g > cap) g = cap;
     if (g < 1) g = 1;
     return (unsigned)g;
+}
+
+// Scan layout for n int32 elements: blocks of per_block elements.
+struct ScanLayout {
+    int64_t per_block, blocks;
+};
+static ScanLayout scan_layout(int64_t n) {
+    ScanLayout L;
+    L.per_block = 8 * kScanBlock;
+    L.blocks = (n + L.per_block - 1) / L.per_block;
+    if (L.blocks < 1) L.blocks = 1;
+    return L;
+}
+
+size_t scan_scratch_bytes(int64_t n) { return up256(8 * (size_t)scan_layout(n).blocks); }
+
+cudaError_t scan_exclusive_i32(int32_t* data, int64_t n, void* scratch, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const ScanLayout L = scan_layout(n);
+    int64_t* sums = static_cast<int64_t*>(scratch);
+    scan_block_sums_kernel<<<(unsigned)L.blocks, 1024, 0, s>>>(data, n, L.per_block, sums);
+    scan_sums_serial_kernel<<<1, 32, 0, s>>>(sums, L.blocks);
+    scan_apply_kernel<<<(unsigned)L.blocks, 1024, 0, s>>>(data, n, L.per_block, sums);
+    return cudaGetLastError();
+}
+
+// Radix scratch: the digit-major count table (256 x tiles) and its scan sums.
+size_t radix_scratch_bytes(int64_t n) {
+    const int64_t ntiles = n > 0 ? (n + kTile - 1) / kTile : 1;
+    const int64_t ncounts = ntiles * kRadix;
+    return up256(4 * (size_t)ncounts) + scan_scratch_bytes(ncounts);
+}
+
+cudaError_t radix_sort_pairs(const int32_t* keys, const int32_t* vals, int64_t n, int key_bits,
+                             int32_t* k0, int32_t* v0, int32_t* k1, int32_t* v1, void* scratch,
+                             int* out, cudaStream_t s) {
+    *out = 0;
+    if (n <= 0) return cudaSuccess;
+    const int64_t ntiles = (n + kTile - 1) / kTile;
+    const int64_t ncounts = ntiles * kRadix;
+    int32_t* counts = static_cast<int32_t*>(scratch);
+    void* sums = static_cast<char*>(scratch) + up256(4 * (size_t)ncounts);
+    int32_t* kb[2] = {k0, k1};
+    int32_t* vb[2] = {v0, v1};
+    const int32_t* kin = keys;
+    const int32_t* vin = vals;   // nullptr: first pass carries the index
+    const int passes = (key_bits + 7) / 8 > 0 ? (key_bits + 7) / 8 : 1;
+    int cur = 0;
+    for (int pass = 0; pass < passes; ++pass) {
+        const int shift = 8 * pass;
+        radix_count_kernel<<<(unsigned)ntiles, kSortThreads, 0, s>>>(kin, n, shift, ntiles, counts);
+        cudaError_t e = scan_exclusive_i32(counts, ncounts, sums, s);
+        if (e != cudaSuccess) return e;
+        radix_scatter_kernel<<<(unsigned)ntiles, kSortThreads, 0, s>>>(kin, vin, n, shift, ntiles,
+                                                                       counts, kb[cur], vb[cur]);
+        kin = kb[cur];
+        vin = vb[cur];
+        *out = cur;
+        cur ^= 1;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t csr_rows_of(const int32_t* rowptr, int64_t M, int32_t* row_of, cudaStream_t s) {
+    if (M <= 0) return cudaSuccess;
+    expand_rows_kernel<<<grid_cap(M * 32, 256), 256, 0, s>>>(rowptr, M, row_of);
+    return cudaGetLastError();
+}
+
+cudaError_t lower_bounds(const int32_t* sorted, int64_t n, int64_t K, int32_t* ptr,
+                         cudaStream_t s) {
+    colptr_kernel<<<grid_cap(K + 1, 256), 256, 0, s>>>(sorted, n, K, ptr);
+    return cudaGetLastError();
+}
+
+int bits_for(int64_t n) {
+    int bits = 1;
+    while (bits < 31 && ((int64_t)1 << bits) < n) ++bits;
+    return bits;
+}
+
+struct TransposeLayout {
+    size_t row_of, keys0, keys1, vals0, vals1, scratch, total;
+};
+
+static TransposeLayout transpose_layout(int64_t nnz) {
+    TransposeLayout L;
+    size_t off = 0;
+    const size_t a = up256(4 * (size_t)(nnz > 0 ? nnz : 1));
+    L.row_of = off; off += a;
+    L.keys0 = off; off += a;
+    L.keys1 = off; off += a;
+    L.vals0 = off; off += a;
+    L.vals1 = off; off += a;
+    L.scratch = off; off += radix_scratch_bytes(nnz);
+    L.total = off;
+    return L;
 }
 
 }  // namespace spmm
@@ -320,28 +393,14 @@ extern "C" int spmm_csr_transpose(const int32_t* A_rowptr, const int32_t* A_coli
     int32_t* row_of = reinterpret_cast<int32_t*>(ws + L.row_of);
     int32_t* kb[2] = {reinterpret_cast<int32_t*>(ws + L.keys0), reinterpret_cast<int32_t*>(ws + L.keys1)};
     int32_t* vb[2] = {reinterpret_cast<int32_t*>(ws + L.vals0), reinterpret_cast<int32_t*>(ws + L.vals1)};
-    int32_t* counts = reinterpret_cast<int32_t*>(ws + L.counts);
-    int64_t* sums = reinterpret_cast<int64_t*>(ws + L.sums);
 
-    expand_rows_kernel<<<grid_cap(M * 32, 256), 256, 0, s>>>(A_rowptr, M, row_of);
-    int bits = 1;
-    while (bits < 31 && ((int64_t)1 << bits) < K) ++bits;
-    const int passes = (bits + 7) / 8;
-    const int32_t* kin = A_colind;
-    const int32_t* vin = nullptr;   // first pass: value = own index
-    int cur = 0;
-    for (int pass = 0; pass < passes; ++pass) {
-        const int shift = 8 * pass;
-        radix_count_kernel<<<(unsigned)L.ntiles, kSortThreads, 0, s>>>(kin, nnz, shift, L.ntiles, counts);
-        scan_block_sums_kernel<<<(unsigned)L.scan_blocks, 1024, 0, s>>>(counts, L.ncounts, L.per_block, sums);
-        scan_sums_serial_kernel<<<1, 32, 0, s>>>(sums, L.scan_blocks);
-        scan_apply_kernel<<<(unsigned)L.scan_blocks, 1024, 0, s>>>(counts, L.ncounts, L.per_block, sums);
-        radix_scatter_kernel<<<(unsigned)L.ntiles, kSortThreads, 0, s>>>(kin, vin, nnz, shift, L.ntiles,
-                                                                          counts, kb[cur], vb[cur]);
-        kin = kb[cur];
-        vin = vb[cur];
-        cur ^= 1;
-    }
+    if (csr_rows_of(A_rowptr, M, row_of, s) != cudaSuccess) return SPMM_ERR_CUDA;
+    int res = 0;
+    if (radix_sort_pairs(A_colind, nullptr, nnz, bits_for(K), kb[0], vb[0], kb[1], vb[1],
+                         ws + L.scratch, &res, s) != cudaSuccess)
+        return SPMM_ERR_CUDA;
+    const int32_t* kin = kb[res];
+    const int32_t* vin = vb[res];
     colptr_kernel<<<grid_cap(K + 1, 256), 256, 0, s>>>(kin, nnz, K, out_colptr);
     const unsigned g = grid_cap(nnz, 256);
     switch (out_vals ? elem_bytes(val_dtype) : 4) {
