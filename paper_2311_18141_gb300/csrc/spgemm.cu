@@ -6,9 +6,10 @@
 //      products; an exclusive scan of the counts gives each its offset.
 //   2. expand: one warp per nonzero of A writes (i, j, A_ik * B_kj) for the
 //      nonzeros (k, j) of B's row k, in A's CSR order and then B's.
-//   3. sort: the products are sorted stably by column, then stably by row
-//      (LSD radix sort carrying each product's index), so equal (i, j) stay in
-//      expansion order.
+//   3. sort: when bits(M) + bits(N) <= 32 the key (i << bits(N)) | j is sorted
+//      once, stably, carrying the value; otherwise the products are sorted
+//      stably by column, then stably by row, carrying each product's index.
+//      Either way equal (i, j) stay in expansion order.
 //   4. compress: runs of equal (i, j) are summed in FP32 in that order, one
 //      entry of C each; row pointers by lower bound over the entry rows.
 // An entry of C exists wherever some product is formed (explicit zeros
@@ -85,6 +86,68 @@ __global__ void spgemm_expand_kernel(const int32_t* __restrict__ A_colind,
             pcol[o + (f - b0)] = j;
             pval[o + (f - b0)] = a * B_vals[f];
         }
+    }
+}
+
+// Fused-key form (bits(M) + bits(N) <= 32): each product's key is
+// (row << bN) | col and its payload the FP32 value, so one stable sort of the
+// keys orders the products by (row, col) with equal pairs in expansion order.
+__global__ void spgemm_expand_fused_kernel(const int32_t* __restrict__ A_colind,
+                                           const float* __restrict__ A_vals,
+                                           const int32_t* __restrict__ row_of,
+                                           const int32_t* __restrict__ off, int64_t nnzA,
+                                           int64_t K, const int32_t* __restrict__ B_rowptr,
+                                           const int32_t* __restrict__ B_colind,
+                                           const float* __restrict__ B_vals, int64_t N, int bN,
+                                           uint32_t* __restrict__ key, float* __restrict__ val,
+                                           int32_t* status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t e = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < nnzA; e += nw) {
+        const int32_t k = A_colind[e];
+        if (k < 0 || k >= K) continue;   // counted as no products
+        const int32_t b0 = B_rowptr[k], b1 = B_rowptr[k + 1];
+        const uint32_t rk = (uint32_t)row_of[e] << bN;
+        const float a = A_vals[e];
+        const int64_t o = off[e];
+        for (int32_t f = b0 + lane; f < b1; f += 32) {
+            int32_t j = B_colind[f];
+            if (j < 0 || j >= N) {
+                atomicCAS(status, 0, SPMM_ERR_BAD_CSR);
+                j = 0;
+            }
+            key[o + (f - b0)] = rk | (uint32_t)j;
+            val[o + (f - b0)] = a * B_vals[f];
+        }
+    }
+}
+
+__global__ void spgemm_heads_fused_kernel(const uint32_t* __restrict__ key, int64_t P,
+                                          int32_t* __restrict__ head) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p <= P; p += stride)
+        head[p] = p < P && (p == 0 || key[p] != key[p - 1]);
+}
+
+__global__ void spgemm_compress_fused_kernel(const uint32_t* __restrict__ key,
+                                             const float* __restrict__ val,
+                                             const int32_t* __restrict__ pos, int64_t P, int bN,
+                                             int32_t* __restrict__ crow, int32_t* __restrict__ ccol,
+                                             float* __restrict__ cval) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += stride) {
+        if (pos[p + 1] == pos[p]) continue;   // not the first product of its run
+        const int32_t q = pos[p];
+        float sum = val[p];
+        int64_t x = p + 1;
+        while (x < P && pos[x + 1] == pos[x]) {
+            sum += val[x];
+            ++x;
+        }
+        const uint32_t kk = key[p];
+        crow[q] = (int32_t)(kk >> bN);
+        ccol[q] = (int32_t)(kk & ((1u << bN) - 1u));
+        cval[q] = sum;
     }
 }
 
@@ -256,6 +319,27 @@ extern "C" int spmm_spgemm(const int32_t* A_rowptr, const int32_t* A_colind, con
         spgemm_count_kernel<<<grid_for(nnzA, 256), 256, 0, s>>>(A_colind, nnzA, B_rowptr, K,
                                                                  I(L.off), status);
         if (scan_exclusive_i32(I(L.off), nnzA, ws + L.scan, s) != cudaSuccess) return SPMM_ERR_CUDA;
+        const int bM = bits_for(M), bN = bits_for(N);
+        if (bM + bN <= 32) {
+            uint32_t* key = reinterpret_cast<uint32_t*>(ws + L.prow);
+            float* val = reinterpret_cast<float*>(ws + L.pval);
+            spgemm_expand_fused_kernel<<<grid_for(nnzA * 32, 256), 256, 0, s>>>(
+                A_colind, A_vals, I(L.row_of), I(L.off), nnzA, K, B_rowptr, B_colind, B_vals, N,
+                bN, key, val, status);
+            int r = 0;
+            if (radix_sort_pairs(reinterpret_cast<const int32_t*>(key),
+                                 reinterpret_cast<const int32_t*>(val), P, bM + bN, I(L.k0),
+                                 I(L.v0), I(L.k1), I(L.v1), ws + L.radix, &r, s) != cudaSuccess)
+                return SPMM_ERR_CUDA;
+            const uint32_t* skey = reinterpret_cast<const uint32_t*>(r ? I(L.k1) : I(L.k0));
+            const float* sval = reinterpret_cast<const float*>(r ? I(L.v1) : I(L.v0));
+            spgemm_heads_fused_kernel<<<grid_for(P + 1, 256), 256, 0, s>>>(skey, P, I(L.pos));
+            if (scan_exclusive_i32(I(L.pos), P + 1, ws + L.radix, s) != cudaSuccess)
+                return SPMM_ERR_CUDA;
+            spgemm_compress_fused_kernel<<<grid_for(P, 256), 256, 0, s>>>(
+                skey, sval, I(L.pos), P, bN, I(L.crow), I(L.ccol),
+                reinterpret_cast<float*>(ws + L.cval));
+        } else {
         spgemm_expand_kernel<<<grid_for(nnzA * 32, 256), 256, 0, s>>>(
             A_colind, A_vals, I(L.row_of), I(L.off), nnzA, K, B_rowptr, B_colind, B_vals, N,
             I(L.prow), I(L.pcol), reinterpret_cast<float*>(ws + L.pval), status);
@@ -279,6 +363,7 @@ extern "C" int spmm_spgemm(const int32_t* A_rowptr, const int32_t* A_colind, con
         spgemm_compress_kernel<<<grid_for(P, 256), 256, 0, s>>>(
             rows, idx, I(L.pcol), reinterpret_cast<const float*>(ws + L.pval), I(L.pos), P,
             I(L.crow), I(L.ccol), reinterpret_cast<float*>(ws + L.cval));
+        }
         if (cudaGetLastError() != cudaSuccess) return SPMM_ERR_CUDA;
     }
     int32_t h_status = 0;

@@ -77,12 +77,28 @@ scan_block_sums_kernel(const int32_t* __restrict__ in, int64_t n, int64_t per_bl
     if (threadIdx.x == 0) sums[blockIdx.x] = red[0];
 }
 
-__global__ void scan_sums_serial_kernel(int64_t* sums, int64_t nb) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    int64_t run = 0;
-    for (int64_t b = 0; b < nb; ++b) {
-        const int64_t v = sums[b];
-        sums[b] = run;
+// Exclusive scan of the nb block sums, in place, by one block of 1024 threads:
+// each thread sums a run of consecutive entries, the 1024 run totals are
+// scanned in shared memory, and each thread writes its run's prefixes.
+__global__ void __launch_bounds__(1024) scan_sums_serial_kernel(int64_t* sums, int64_t nb) {
+    __shared__ int64_t part[1024];
+    const int64_t per = (nb + 1023) / 1024;
+    const int64_t a = min(nb, (int64_t)threadIdx.x * per);
+    const int64_t b = min(nb, a + per);
+    int64_t s = 0;
+    for (int64_t i = a; i < b; ++i) s += sums[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const int64_t v = (int)threadIdx.x >= off ? part[threadIdx.x - off] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int64_t run = threadIdx.x ? part[threadIdx.x - 1] : 0;
+    for (int64_t i = a; i < b; ++i) {
+        const int64_t v = sums[i];
+        sums[i] = run;
         run += v;
     }
 }
@@ -281,7 +297,7 @@ cudaError_t scan_exclusive_i32(int32_t* data, int64_t n, void* scratch, cudaStre
     const ScanLayout L = scan_layout(n);
     int64_t* sums = static_cast<int64_t*>(scratch);
     scan_block_sums_kernel<<<(unsigned)L.blocks, 1024, 0, s>>>(data, n, L.per_block, sums);
-    scan_sums_serial_kernel<<<1, 32, 0, s>>>(sums, L.blocks);
+    scan_sums_serial_kernel<<<1, 1024, 0, s>>>(sums, L.blocks);
     scan_apply_kernel<<<(unsigned)L.blocks, 1024, 0, s>>>(data, n, L.per_block, sums);
     return cudaGetLastError();
 }

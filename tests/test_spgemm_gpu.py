@@ -93,3 +93,20 @@ def test_column_out_of_range_is_reported():
     with pytest.raises(binding.SpmmError) as e:
         binding.spgemm(a[0], a[1], a[2], 1, 2, b[0], b[1], b[2], 1)
     assert e.value.status == binding.SPMM_ERR_BAD_CSR
+
+
+def test_wide_shapes_take_the_two_sort_path():
+    # bits(M) + bits(N) > 32: products are sorted by column, then by row
+    rng = np.random.default_rng(9)
+    M, K, N = 100_000, 64, 90_000
+    a_rows = rng.integers(0, 3, M)
+    a_rp = np.zeros(M + 1, np.int64)
+    a_rp[1:] = np.cumsum(a_rows)
+    a_ci = np.concatenate([np.sort(rng.choice(K, n, replace=False)) for n in a_rows]).astype(np.int32)
+    b_rows = rng.integers(0, 6, K)
+    b_rp = np.zeros(K + 1, np.int64)
+    b_rp[1:] = np.cumsum(b_rows)
+    b_ci = np.concatenate([np.sort(rng.choice(N, n, replace=False)) for n in b_rows]).astype(np.int32)
+    a = (a_rp.astype(np.int32), a_ci, rng.standard_normal(a_ci.size).astype(np.float32))
+    b = (b_rp.astype(np.int32), b_ci, rng.standard_normal(b_ci.size).astype(np.float32))
+    _check(a, b, M, K, N)
