@@ -677,13 +677,19 @@ def run_spgemm(args):
     _, _, bound = oracle.spgemm(rph, cih, np.abs(vh), rph, cih, np.abs(vh), M, M)
     rel = np.abs(v.cpu().numpy().astype(np.float64) - ev) / np.maximum(bound, 1e-30)
     bytes_min = 4 * (M + 1) + 8 * nnz + 4 * (M + 1) + 8 * E.value   # A once, C once
+    context = None
+    if args.context:   # cuSPARSE SpGEMM through torch.sparse.mm, as context only
+        At = torch.sparse_csr_tensor(A.rowptr.long(), A.colind.long(), A.vals, size=(M, M))
+        ctx_ms = _time_ms(lambda: torch.sparse.mm(At, At), max(3, args.steps), 2, stream)
+        context = {"torch_sparse_mm_ms": ctx_ms,
+                   "what": "cuSPARSE SpGEMM through torch.sparse.mm on the same A (context only)"}
     print(json.dumps({"workload": f"spgemm-rmat-s{args.spgemm_scale}-AxA", "nnz": nnz,
                       "products": P.value, "entries": E.value, "ms": ms,
                       "gflops": 2.0 * P.value / (ms * 1e-3) / 1e9,
                       "products_per_s": P.value / (ms * 1e-3),
                       "structure_matches_oracle": structure_ok,
                       "err_max": float(rel.max()) if rel.size else 0.0,
-                      "min_bytes": bytes_min}), flush=True)
+                      "min_bytes": bytes_min, "context": context}), flush=True)
 
 
 def main():
