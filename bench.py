@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--spgemm-scale", type=int, default=14,
                     help="R-MAT scale of the A*A SpGEMM workload")
     ap.add_argument("--workload", default="rmat",
-                    choices=["rmat", "precision", "gcn", "batch", "spgemm"],
+                    choices=["rmat", "precision", "gcn", "batch", "spgemm", "loadsim"],
                     help="rmat: the benchmark line; the others report the precision, "
                          "backward and batched forms")
     return ap.parse_args()
@@ -692,8 +692,33 @@ def run_spgemm(args):
                       "min_bytes": bytes_min, "context": context}), flush=True)
 
 
+def run_loadsim(args):
+    """Fig. 1's analysis on the host: R-MAT scale 17, edge factor 8, a = 0.6,
+    b = c = d = 0.4/3, squared on a 16 x 16 grid -- end-to-end vs synchronised
+    load imbalance, as generated and after one random symmetric relabelling;
+    then the SpMM tile grids of the benchmark's shape (N = 128) on the same A."""
+    import numpy as np
+    from paper_2311_18141_gb300 import inputs, loadsim
+    A = inputs.rmat_csr(17, 8, 0.6, 0.4 / 3, 0.4 / 3, seed=1, device="cpu", values="pos")
+    rp, ci = A.rowptr.numpy(), A.colind.numpy()
+    out = {"workload": "loadsim-rmat-s17-ef8-a0.6-16x16", "nnz": A.nnz}
+    for name, (r, c) in (("as_generated", (rp, ci)),
+                         ("relabelled", loadsim.relabel(rp, ci, np.random.default_rng(0).permutation(A.M)))):
+        im = loadsim.imbalance(loadsim.spgemm_stage_work(r, c, r, c, A.K, A.K, 16))
+        out[name] = {"spgemm_end_to_end": im.end_to_end, "spgemm_synchronised": im.synchronised,
+                     "spgemm_worst_stage": float(im.per_stage.max())}
+        for TR, TC in ((16, 4), (16, 1), (4, 4)):
+            imm = loadsim.imbalance(loadsim.spmm_stage_work(r, c, A.K, 128, TR, TC, 16))
+            out[name][f"spmm_{TR}x{TC}_end_to_end"] = imm.end_to_end
+            out[name][f"spmm_{TR}x{TC}_synchronised"] = imm.synchronised
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "loadsim":
+        run_loadsim(args)
+        return
     if args.workload == "spgemm":
         run_spgemm(args)
         return
