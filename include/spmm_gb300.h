@@ -97,8 +97,11 @@ int spmm_version(void);
  *   Section 2.1 tiles C into a grid of row blocks x column blocks; Section 3.4
  *   (Algorithm 3) reserves work inside a tile with fetch-and-add.  The plan
  *   splits each C row block's merge path (its rows interleaved with its
- *   nonzeros) into equal runs of `chunk_items` items; every (chunk, column
- *   block) pair is one work unit, so a heavy row is shared by several units.
+ *   nonzeros) into runs ("chunks") of about `chunk_items` items; a boundary
+ *   inside a row of fewer than chunk_items/8 items moves to the row's start.
+ *   The kernel reserves, in one column block, 32/LPN consecutive chunks at a
+ *   time (LPN lanes hold one column block of a B row), one per lane group;
+ *   a heavy row is shared by several chunks.
  *   A_rowptr  device int32[M+1], read on `stream` during this call.
  *   M, K, nnz, N  problem shape (N = columns of B and C).
  *   tile_rows, tile_cols  grid shape, 1 <= tile_rows <= 65536,
@@ -119,7 +122,8 @@ int spmm_plan_destroy(spmm_plan plan);
 /* Bytes of per-call scratch a call with this plan needs (host out-param). */
 int spmm_plan_workspace_size(spmm_plan plan, size_t* bytes);
 
-/* Number of work units (chunks x column blocks) of a plan, for reporting. */
+/* Chunks of a plan and chunks x column blocks (the (chunk, tile) pairs), for
+ * reporting. */
 int spmm_plan_units(spmm_plan plan, int64_t* chunks, int64_t* units);
 
 /* Bytes of workspace a spmm_csr call with plan == NULL needs: the plan arrays
@@ -182,10 +186,11 @@ typedef struct spmm_batch_s* spmm_batch;
 /*
  * spmm_batch_create -- plans for `count` independent products run as one
  *   persistent launch.  The batch form of Section 3.4's reservation: every
- *   product keeps its own merge-path plan, its (chunk, column block) units are
- *   numbered after those of the products before it, and the warps of one grid
- *   reserve units from a single counter, so warps that finish one product move
- *   on to any other.  Products run largest first.  All products share A's value
+ *   product keeps its own merge-path plan, its units (32/LPN chunks in one
+ *   column block) are numbered after those of the products before it, and the
+ *   warps of one grid reserve units from a single counter, so warps that finish
+ *   one product move on to any other.  Products run by width (so the warps of an
+ *   SM mostly share one kernel shape), each width largest first.  All products share A's value
  *   type `a_dtype` and B's type `b_dtype`.  `problems` is a host array copied at
  *   creation; the device arrays it points to must stay valid while the batch is
  *   used.  Allocates device memory for plans and the descriptor table and
@@ -196,7 +201,7 @@ int spmm_batch_create(spmm_batch* batch, const spmm_problem* problems, int32_t c
 int spmm_batch_destroy(spmm_batch batch);
 
 /* Workspace bytes for spmm_csr_batched / spmm_batch_graph_launch under any
- * shapes spmm_batch_autotune may choose (chunks of at least 512 items, at most
+ * shapes spmm_batch_autotune may choose (chunks of at least 256 items, at most
  * two column blocks, up to 16 row blocks). */
 int spmm_batch_workspace_size(spmm_batch batch, size_t* bytes);
 
@@ -217,7 +222,7 @@ int spmm_csr_batched(spmm_batch batch, void* workspace, size_t workspace_bytes, 
 int spmm_batch_graph_launch(spmm_batch batch, void* workspace, size_t workspace_bytes,
                             void* stream);
 
-/* Choose row blocks {1,4}, column blocks {1,2} and chunk size {512..4096} per
+/* Choose row blocks {1,4}, column blocks {1,2} and chunk size {256..2048} per
  * size class (same N, rows below 10k / 50k / above) by coordinate descent,
  * timing `reps` batched launches per candidate with CUDA events; leaves the
  * batch planned with the best shapes and returns the best time in *best_ms. */
