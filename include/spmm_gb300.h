@@ -304,6 +304,57 @@ int spmm_spgemm_copy(const void* workspace, int64_t M, int64_t nnzA, int64_t pro
 int spmm_get_device_status(void* workspace, int32_t* status, void* stream);
 
 /*
+ * Host-buffer pipeline -- the local product C = A B of Section 2.1 for
+ * operands that live in host memory, one product per submitted step.  Each
+ * step copies A (rowptr, colind, vals) and B from the host to the device,
+ * runs spmm_csr with the pipeline's plan, and copies C back to the host.  The
+ * pipeline owns `depth` device slots (one set of A, B and C arrays each), one
+ * workspace and two streams of its own (copy-in, copy-out); the products run
+ * on the caller's `stream`.  Step k uses slot k mod depth: its inputs copy in
+ * once the product of step k - depth has finished reading that slot, and its
+ * product starts once step k - depth's C has left the slot.  With depth >= 2
+ * the upload of step k+1 and the download of step k-1 overlap the product of
+ * step k, the way the paper's prefetching overlaps tile transfers with local
+ * multiplies (Section 3.3).  depth = 1 runs the steps one after the other.
+ */
+typedef struct spmm_host_pipe_s* spmm_host_pipe;
+
+/*
+ * spmm_host_pipe_create -- allocate a pipeline for `plan`'s shape (M, K, nnz,
+ *   N and tile grid): depth (1..4) slots of (M+1) + nnz int32, nnz elements
+ *   of a_dtype, K x N elements of b_dtype (dense, ldb = N) and M x N float
+ *   (ldc = N), plus the plan's workspace.  N must meet the vector-path rule of
+ *   b_dtype.  The plan must outlive the pipeline.  Allocates device memory and
+ *   creates two streams and 3 * depth events; *pipe is NULL on failure.
+ */
+int spmm_host_pipe_create(spmm_host_pipe* pipe, spmm_plan plan, int32_t a_dtype,
+                          int32_t b_dtype, int32_t depth, void* stream);
+
+/*
+ * spmm_host_pipe_submit -- enqueue one step: A_rowptr int32[M+1], A_colind
+ *   int32[nnz], A_vals (a_dtype)[nnz] and B (b_dtype)[K*N] are host inputs;
+ *   C float[M*N] receives A B (host).  All five are host pointers.  The call
+ *   only enqueues work and returns: the inputs must stay unchanged and C
+ *   unread until spmm_host_pipe_wait returns.  The copies overlap other work
+ *   only when the host buffers are page-locked (cudaHostAlloc or
+ *   cudaHostRegister); pageable buffers are copied synchronously.
+ */
+int spmm_host_pipe_submit(spmm_host_pipe pipe, const int32_t* A_rowptr, const int32_t* A_colind,
+                          const void* A_vals, const void* B, float* C);
+
+/*
+ * spmm_host_pipe_wait -- block until every submitted step's C is in host
+ *   memory.  Returns SPMM_OK, SPMM_ERR_CUDA, or the first error a product's
+ *   device code reported (e.g. SPMM_ERR_TIMEOUT, SPMM_ERR_INTERNAL), which it
+ *   then clears.
+ */
+int spmm_host_pipe_wait(spmm_host_pipe pipe);
+
+/* spmm_host_pipe_destroy -- wait for outstanding steps, then free the slots,
+ * the workspace, the streams and the events.  NULL is a no-op. */
+int spmm_host_pipe_destroy(spmm_host_pipe pipe);
+
+/*
  * spmm_csr_transpose -- CSR of A (M x K) -> CSR of A^T (K x M), i.e. A's CSC.
  *   Needed by the backward pass dB = A^T dC.  Built on the device by a stable
  *   least-significant-digit radix sort of the nonzeros by column, so each

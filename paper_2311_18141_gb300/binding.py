@@ -38,7 +38,8 @@ EXPORTED = [
     "spmm_csr_noalloc", "spmm_batch_create", "spmm_batch_destroy", "spmm_batch_workspace_size",
     "spmm_batch_set_shapes", "spmm_batch_get_shapes", "spmm_csr_batched",
     "spmm_batch_graph_launch", "spmm_batch_autotune", "spmm_spgemm_analyze", "spmm_spgemm",
-    "spmm_spgemm_copy",
+    "spmm_spgemm_copy", "spmm_host_pipe_create", "spmm_host_pipe_submit", "spmm_host_pipe_wait",
+    "spmm_host_pipe_destroy",
 ]
 
 
@@ -115,6 +116,10 @@ def load_library(path: str | None = None):
         lib.spmm_csr_batched.argtypes = [vp, vp, sz, vp]
         lib.spmm_batch_graph_launch.argtypes = [vp, vp, sz, vp]
         lib.spmm_batch_autotune.argtypes = [vp, vp, sz, i32, vp, P(ctypes.c_float)]
+        lib.spmm_host_pipe_create.argtypes = [P(vp), vp, i32, i32, i32, vp]
+        lib.spmm_host_pipe_submit.argtypes = [vp, vp, vp, vp, vp, vp]
+        lib.spmm_host_pipe_wait.argtypes = [vp]
+        lib.spmm_host_pipe_destroy.argtypes = [vp]
         lib.spmm_csr_noalloc.argtypes = [vp, vp, vp, i32, vp, vp, i32, vp, i64, vp, i64, i64, i64,
                                          i64, i64, i32, i32, f32, vp]
         for name in EXPORTED:
@@ -197,6 +202,43 @@ class Plan:
     def close(self):
         if self.handle:
             load_library().spmm_plan_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class HostPipe:
+    """Owner of a spmm_host_pipe (host-buffer pipeline over a plan): submit()
+    enqueues one product of host tensors A (rowptr, colind, vals), B into host
+    C; wait() blocks until every submitted C is in host memory."""
+
+    def __init__(self, plan: Plan, a_dtype: torch.dtype, b_dtype: torch.dtype, depth: int = 2,
+                 stream=None):
+        self.plan = plan   # the pipeline uses the plan: keep it alive
+        self.handle = ctypes.c_void_p()
+        _check(load_library().spmm_host_pipe_create(ctypes.byref(self.handle), plan.handle,
+                                                    dtype_code(a_dtype), dtype_code(b_dtype),
+                                                    int(depth), _stream(stream)),
+               "spmm_host_pipe_create")
+
+    def submit(self, rowptr, colind, vals, B, C) -> None:
+        for t in (rowptr, colind, vals, B, C):
+            if t.is_cuda or not t.is_contiguous():
+                raise ValueError("host pipeline operands are contiguous host tensors")
+        _check(load_library().spmm_host_pipe_submit(self.handle, _ptr(rowptr), _ptr(colind),
+                                                    _ptr(vals), _ptr(B), _ptr(C)),
+               "spmm_host_pipe_submit")
+
+    def wait(self) -> None:
+        _check(load_library().spmm_host_pipe_wait(self.handle), "spmm_host_pipe_wait")
+
+    def close(self):
+        if self.handle:
+            load_library().spmm_host_pipe_destroy(self.handle)
             self.handle = ctypes.c_void_p()
 
     def __del__(self):

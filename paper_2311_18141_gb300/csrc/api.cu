@@ -102,6 +102,18 @@ int plan_view(spmm_plan plan, int64_t M, int64_t K, int64_t nnz, int64_t N, int3
     return SPMM_OK;
 }
 
+int plan_shape(spmm_plan plan, int64_t* M, int64_t* K, int64_t* nnz, int64_t* N, int32_t* TR,
+               int32_t* TC) {
+    if (!plan) return SPMM_ERR_INVALID_ARG;
+    if (M) *M = plan->M;
+    if (K) *K = plan->K;
+    if (nnz) *nnz = plan->nnz;
+    if (N) *N = plan->N;
+    if (TR) *TR = plan->TR;
+    if (TC) *TC = plan->TC;
+    return SPMM_OK;
+}
+
 }  // namespace spmm
 
 extern "C" {

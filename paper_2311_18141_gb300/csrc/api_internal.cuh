@@ -15,5 +15,8 @@ int device_sm_count();
 int plan_view(spmm_plan plan, int64_t M, int64_t K, int64_t nnz, int64_t N, int32_t* TR,
               int32_t* TC, int32_t* RB, int32_t* D, int64_t* cap, int32_t** blk_base,
               int32_t** bnd_row, int32_t** bnd_nnz);
+// Shape of a plan (any output may be null).
+int plan_shape(spmm_plan plan, int64_t* M, int64_t* K, int64_t* nnz, int64_t* N, int32_t* TR,
+               int32_t* TC);
 
 }  // namespace spmm

@@ -94,6 +94,20 @@ def test_host_argument_checks_return_before_device_work(lib):
     # validate needs a workspace for its status word
     assert lib.spmm_csr_validate(fake, fake, 4, 4, 4, None, 0,
                                  None) == binding.SPMM_ERR_WORKSPACE
+    # host pipeline: null handles and plans are rejected, destroy(NULL) is a no-op
+    h = ctypes.c_void_p()
+    assert lib.spmm_host_pipe_create(ctypes.byref(h), None, 0, 0, 2,
+                                     None) == binding.SPMM_ERR_INVALID_ARG
+    assert not h.value
+    assert lib.spmm_host_pipe_create(None, fake, 0, 0, 2, None) == binding.SPMM_ERR_INVALID_ARG
+    assert lib.spmm_host_pipe_create(ctypes.byref(h), fake, 0, 0, 0,
+                                     None) == binding.SPMM_ERR_INVALID_ARG
+    assert lib.spmm_host_pipe_create(ctypes.byref(h), fake, 7, 0, 2,
+                                     None) == binding.SPMM_ERR_UNSUPPORTED
+    assert lib.spmm_host_pipe_submit(None, fake, fake, fake, fake,
+                                     fake) == binding.SPMM_ERR_INVALID_ARG
+    assert lib.spmm_host_pipe_wait(None) == binding.SPMM_ERR_INVALID_ARG
+    assert lib.spmm_host_pipe_destroy(None) == binding.SPMM_OK
 
 
 def test_workspace_size_grows_with_problem(lib):
