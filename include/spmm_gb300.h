@@ -19,10 +19,12 @@
  *     default stream.  All device work is enqueued asynchronously on it; the
  *     calls do not synchronise unless documented.
  *   - Dense matrices are row-major with a leading dimension in ELEMENTS
- *     (ldb >= N, ldc >= N).  Vector paths need B, C, ldb*elem_size and
- *     ldc*4 to be 16-byte aligned and N a multiple of the elements in 16 bytes
- *     of B's type (4 for F32, 8 for F16/BF16, 16 for E4M3); otherwise the call
- *     returns SPMM_ERR_MISALIGNED and enqueues nothing.
+ *     (ldb >= N, ldc >= N, and a row stride below 2^32 bytes: larger
+ *     strides return SPMM_ERR_INVALID_ARG).  Vector paths need B, C,
+ *     ldb*elem_size and ldc*4 to be 16-byte aligned and N a multiple of the
+ *     elements in 16 bytes of B's type (4 for F32, 8 for F16/BF16, 16 for
+ *     E4M3); otherwise the call returns SPMM_ERR_MISALIGNED and enqueues
+ *     nothing.
  *   - Indices are int32; nnz < 2^31.  CSR rows may be in any column order and
  *     may repeat a column (repeats are summed); rowptr must be non-decreasing
  *     with rowptr[0] = 0 and rowptr[M] = nnz, and every column index must lie

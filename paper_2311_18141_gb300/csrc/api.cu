@@ -231,6 +231,9 @@ int spmm_csr(const int32_t* A_rowptr, const int32_t* A_colind, const void* A_val
     if (M == 0 || N == 0) return SPMM_OK;
     if (!A_rowptr || !C || (nnz > 0 && (!A_colind || !A_vals || !B))) return SPMM_ERR_INVALID_ARG;
     if (ldb < N || ldc < N) return SPMM_ERR_INVALID_ARG;
+    // the kernels keep row strides in bytes as 32-bit values
+    if (ldb * elem_bytes(b_dtype) >= ((int64_t)1 << 32) || ldc * 4 >= ((int64_t)1 << 32))
+        return SPMM_ERR_INVALID_ARG;
     const int eb = elem_bytes(b_dtype);
     const int epv = 16 / eb;
     if (N % epv != 0 || (ldb * eb) % 16 != 0 || (ldc * 4) % 16 != 0 || !aligned16(C) ||

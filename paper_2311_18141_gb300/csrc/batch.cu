@@ -160,6 +160,8 @@ int check_problem(const spmm_problem& q, int b_dtype) {
     if (!q.rowptr || !q.C || (q.nnz > 0 && (!q.colind || !q.vals || !q.B)))
         return SPMM_ERR_INVALID_ARG;
     if (q.ldb < q.N || q.ldc < q.N) return SPMM_ERR_INVALID_ARG;
+    if (q.ldb * elem_bytes(b_dtype) >= ((int64_t)1 << 32) || q.ldc * 4 >= ((int64_t)1 << 32))
+        return SPMM_ERR_INVALID_ARG;
     const int eb = elem_bytes(b_dtype);
     const int epv = 16 / eb;
     if (q.N % epv != 0 || (q.ldb * eb) % 16 != 0 || (q.ldc * 4) % 16 != 0 ||

@@ -348,6 +348,8 @@ extern "C" int spmm_sddmm_csr(const int32_t* A_rowptr, const int32_t* A_colind, 
     if (!A_rowptr || !A_colind || !dC || !B || !out_vals) return SPMM_ERR_INVALID_ARG;
     if (N == 0) return SPMM_ERR_INVALID_ARG;
     if (lddc < N || ldb < N) return SPMM_ERR_INVALID_ARG;
+    if (ldb * elem_bytes(b_dtype) >= ((int64_t)1 << 32) || lddc * 4 >= ((int64_t)1 << 32))
+        return SPMM_ERR_INVALID_ARG;
     const int eb = elem_bytes(b_dtype);
     const int epv = 16 / eb;
     if (N % epv != 0 || (ldb * eb) % 16 != 0 || (lddc * 4) % 16 != 0 ||

@@ -76,6 +76,13 @@ def test_host_argument_checks_return_before_device_work(lib):
     rc = lib.spmm_csr(fake, fake, fake, 0, None, fake, 0, None, 6, fake, 6, 8, 8, 6, 8, 1, 1,
                       0.0, None, fake, 1 << 20, None)
     assert rc == binding.SPMM_ERR_MISALIGNED
+    # a B row stride of 2^32 bytes or more (the kernels keep strides in 32 bits)
+    rc = lib.spmm_csr(fake, fake, fake, 0, None, fake, 0, None, 1 << 30, fake, 8, 8, 8, 8, 8, 1,
+                      1, 0.0, None, fake, 1 << 20, None)
+    assert rc == binding.SPMM_ERR_INVALID_ARG
+    rc = lib.spmm_csr(fake, fake, fake, 0, None, fake, 0, None, 8, fake, 1 << 30, 8, 8, 8, 8, 1,
+                      1, 0.0, None, fake, 1 << 20, None)
+    assert rc == binding.SPMM_ERR_INVALID_ARG
     # tile grid that leaves a column block empty
     rc = lib.spmm_csr(fake, fake, fake, 0, None, fake, 0, None, 8, fake, 8, 8, 8, 8, 8, 1, 4,
                       0.0, None, fake, 1 << 20, None)
