@@ -185,6 +185,18 @@ def min_bytes(M, K, N, nnz, w_val=4, w_b=4, w_c=4):
     return 4 * (M + 1) + nnz * (4 + w_val) + K * N * w_b + M * N * w_c
 
 
+def tile_nnz_imbalance(rowptr, M: int, TR: int) -> float:
+    """max/avg nonzeros per tile of a TR x TC grid (the load-imbalance figure of
+    the evaluation, Section 6): every column block of a row block holds the
+    row block's nonzeros, so the ratio is the one over row blocks."""
+    rb = -(-M // TR)
+    cuts = [min(i * rb, M) for i in range(TR + 1)]
+    rp = rowptr.cpu() if hasattr(rowptr, "cpu") else rowptr
+    per = [int(rp[cuts[i + 1]]) - int(rp[cuts[i]]) for i in range(TR)]
+    avg = sum(per) / TR
+    return max(per) / avg if avg > 0 else 1.0
+
+
 def cpu_oracle_sample(A, B, seconds: float):
     """Time the FP64 oracle on a stride sample of rows, growing it until about
     `seconds` of CPU work; returns (GFLOP/s, cores, description)."""
@@ -414,6 +426,7 @@ def run_ours(args):
             "config": {"workload": workload_label(args, N),
                        "M": M, "K": K, "N": N, "nnz": nnz, "tile_grid": args.grid,
                        "chunks": chunks, "work_units": units, "tile_order": args.order,
+                       "tile_nnz_max_over_avg": tile_nnz_imbalance(A.rowptr, M, TR),
                        "parallelism": f"replicas x{world}" if world > 1 else "1 gpu",
                        "l2": "inputs larger than L2 (A+B+C = %.2f GB per step)" % (algo_bytes / 1e9)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -82,3 +82,30 @@ def test_single_rank_throughput_needs_no_process_group():
     ms, value = bench.job_throughput(10.0, 5, 4e9, 1, "cpu")
     assert ms == pytest.approx(2.0)
     assert value == pytest.approx(4e9 / 2e-3 / 1e9)
+
+
+def test_minimum_bytes_and_flops_match_hand_computed_values():
+    """The local-SpMM byte count of Section 4 at p = 1 (CSR read once, B read
+    once, C written once) and 2*nnz*N flops, against values worked out by hand
+    for the R-MAT scale-22 workload (nnz 65,245,304, N = 128) and its N = 256
+    storage variants with FP16 values."""
+    M = K = 4194304
+    nnz = 65245304
+    # 4(M+1) + 8 nnz + 4 K N + 4 M N = 16,777,220 + 521,962,432 + 2 * 2,147,483,648
+    assert bench.min_bytes(M, K, 128, nnz) == 4833706948
+    assert 2.0 * nnz * 128 == 16702797824.0
+    # FP16 values (2 bytes), N = 256; CSR part 16,777,220 + 6 nnz = 408,249,044 and
+    # C = 4,294,967,296.  B in FP32 / BF16 / E4M3 is 4,294,967,296 / 2,147,483,648 /
+    # 1,073,741,824 bytes, E4M3 plus 16,777,216 bytes of row scales.
+    assert bench.min_bytes(M, K, 256, nnz, w_val=2, w_b=4) == 8998183636
+    assert bench.min_bytes(M, K, 256, nnz, w_val=2, w_b=2) == 6850699988
+    assert bench.min_bytes(M, K, 256, nnz, w_val=2, w_b=1) + 4 * K == 5793735380
+
+
+def test_tile_imbalance_is_max_over_mean_of_row_blocks():
+    rowptr = torch.tensor([0, 5, 5, 6, 6, 6, 10, 10, 12], dtype=torch.int32)   # M = 8
+    # 4 row blocks of 2 rows: 5, 1, 4, 2 nonzeros -> max 5 / mean 3
+    assert abs(bench.tile_nnz_imbalance(rowptr, 8, 4) - 5 / 3) < 1e-12
+    # ragged: 3 blocks of ceil(8/3) = 3 rows: 6, 4, 2 -> 6 / 4
+    assert abs(bench.tile_nnz_imbalance(rowptr, 8, 3) - 1.5) < 1e-12
+    assert bench.tile_nnz_imbalance(torch.zeros(9, dtype=torch.int32), 8, 4) == 1.0
