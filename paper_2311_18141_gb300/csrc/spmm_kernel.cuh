@@ -120,6 +120,8 @@ struct LaneCols {
     const char* b;         // B + this lane's vector 0 (bytes), clamped into the block
     uint32_t ldb_bytes;    // B row stride in bytes (N <= 2^20, so it fits 32 bits)
     int32_t c_off;         // element offset of this lane's vector 0 within a C row
+    uint32_t ldc_bytes;    // C row stride in bytes (below 2^32)
+    float* c;              // C + this lane's vector 0 in row 0
     uint32_t vmask;        // bit q set when vector q lies inside the column block
     uint32_t qoff[NV];     // byte offset of vector q from b (0 when clamped)
 };
@@ -140,6 +142,8 @@ __device__ __forceinline__ LaneCols<NV> lane_cols(const Problem& p, int j, int t
     lc.b = reinterpret_cast<const char*>(p.B) + cb * K::ESZ;
     lc.ldb_bytes = (uint32_t)(p.ldb * K::ESZ);
     lc.c_off = (int32_t)c0;
+    lc.ldc_bytes = (uint32_t)(p.ldc * 4);
+    lc.c = p.C + c0;
 #pragma unroll
     for (int q = 0; q < NV; ++q)
         lc.qoff[q] = ((lc.vmask >> q) & 1u) ? (uint32_t)(q * STRIDE * 16) : 0u;
@@ -157,9 +161,10 @@ __device__ __forceinline__ const char* brow(const LaneCols<NV>& lc, int col) {
 template <class K, int NV, int STRIDE>
 __device__ __forceinline__ void store_vecs(const Problem& p, int64_t r, const float2* acc,
                                            const LaneCols<NV>& lc) {
-    float sa = 1.0f;
-    if (p.a_scale) sa = __ldg(p.a_scale + r);
-    float* dst = p.C + r * p.ldc + lc.c_off;
+    const bool scaled = p.a_scale != nullptr;
+    const float sa = scaled ? __ldg(p.a_scale + r) : 1.0f;
+    float* dst = reinterpret_cast<float*>(reinterpret_cast<char*>(lc.c) +
+                                          (uint64_t)(uint32_t)r * lc.ldc_bytes);
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
         if (!((lc.vmask >> q) & 1u)) continue;
@@ -168,7 +173,13 @@ __device__ __forceinline__ void store_vecs(const Problem& p, int64_t r, const fl
             float* d = dst + q * STRIDE * K::EPV + h * 4;
             const float2 lo = acc[q * (K::EPV / 2) + 2 * h];
             const float2 hi = acc[q * (K::EPV / 2) + 2 * h + 1];
-            float4 o = make_float4(lo.x * sa, lo.y * sa, hi.x * sa, hi.y * sa);
+            float4 o = make_float4(lo.x, lo.y, hi.x, hi.y);
+            if (scaled) {
+                o.x *= sa;
+                o.y *= sa;
+                o.z *= sa;
+                o.w *= sa;
+            }
             if (p.beta != 0.0f) {
                 const float4 old = __ldcg(reinterpret_cast<const float4*>(d));
                 o.x = fmaf(p.beta, old.x, o.x);
@@ -270,7 +281,6 @@ struct ItemBatch {
     float val[K::IPL];    // its value, times b_scale[col] (0 for other items)
     uint32_t ends;        // bit t: item t ends a row
     uint32_t nz;          // bit t: item t is a nonzero
-    int rbase;            // row that the batch's first row-end item closes
 };
 
 // OR of a per-lane MB-bit mask over the lanes of each group.
@@ -355,7 +365,7 @@ __device__ __forceinline__ bool walk_unit(const Problem& p, int i, int j, int cs
     load_page(2, pg_nx2);
     int pq = 2;
 
-    int beta = 0, e = y0, r = x0;   // next batch: first item, first nonzero, first row
+    int beta = 0, e = y0;   // next batch: first item, first nonzero
     auto decode = [&](ItemBatch<K>& B) {
         uint32_t m = 0;
 #pragma unroll
@@ -387,8 +397,6 @@ __device__ __forceinline__ bool walk_unit(const Problem& p, int i, int j, int cs
         }
         B.ends = m;
         B.nz = nz;
-        B.rbase = r;
-        r += __popc(m);
         e += __popc(nz);
         beta += MB;
         // A batch closes at most MB rows, so at most one page runs out per batch.
@@ -407,6 +415,8 @@ __device__ __forceinline__ bool walk_unit(const Problem& p, int i, int j, int cs
     float2 acc[K::NE / 2];
 #pragma unroll
     for (int q = 0; q < K::NE / 2; ++q) acc[q] = make_float2(0.0f, 0.0f);
+    // items are summed in merge order, so the next row end closes row cur_row
+    int cur_row = x0;
 
     // Accumulate item tt of a batch from its B vectors v[q]; a row-end item
     // then writes its row (the tail piece: its slot).
@@ -415,7 +425,7 @@ __device__ __forceinline__ bool walk_unit(const Problem& p, int i, int j, int cs
 #pragma unroll
         for (int q = 0; q < VPL; ++q) fma_vec<typename K::TB>(acc + q * (K::EPV / 2), a2, v[q]);
         if ((X.ends >> tt) & 1u) {
-            const int row = X.rbase + __popc(X.ends & ((1u << tt) - 1u));
+            const int row = cur_row++;
             if (row == tail_row) store_slot<K>(p, 2 * (int64_t)gc, acc, lc);
             else store_vecs<K, VPL, LPN>(p, row, acc, lc);
 #pragma unroll
