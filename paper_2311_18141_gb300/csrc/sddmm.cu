@@ -3,9 +3,11 @@
 // This is the gradient of sum(dC .* (A B)) with respect to A's values.  It uses
 // the SpMM plan with one column block (a lane group covers the whole row of B),
 // the same per-tile reservation and stealing loop, and the same per-group walk
-// over merge-path sub-chunks, with both the B row and the dC row of every
-// nonzero staged through shared memory by cp.async.  Every output is one
-// nonzero, so rows cut by sub-chunk boundaries need no fix-up.
+// over merge-path sub-chunks.  The B row of every nonzero is staged through
+// shared memory by cp.async; a dC row is staged once per row, with the row's
+// first nonzero, and kept in registers for the rest of the row (shapes whose
+// dC slice would take more than two float4 per lane stage it per nonzero).  Every output
+// is one nonzero, so rows cut by sub-chunk boundaries need no fix-up.
 #include <string.h>
 
 #include "api_internal.cuh"
@@ -21,9 +23,10 @@ struct SddmmProblem {
     float* out;
 };
 
-// Staging shape of the SDDMM walk: each nonzero item stages its B row
-// segment (VPL vectors per lane) and its dC row segment (VPL*DV float4 per
-// lane), SS items per stage, two stages per warp.
+// Staging shape of the SDDMM walk: each nonzero item has slots for its B row
+// segment (VPL vectors per lane) and a dC row segment (VPL*DV float4 per lane;
+// filled only for the first nonzero of a row), SS items per stage, two stages
+// per warp.
 template <class K>
 struct SCfg {
     static constexpr int DV = K::EPV / 4;                       // dC float4s per B vector
@@ -33,6 +36,9 @@ struct SCfg {
     static constexpr int SPB = K::MB / SS;
     static constexpr int STAGE = SS * SLOTS * 32 * 16;           // bytes of one stage buffer
     static constexpr int STAGE_BYTES = 2 * STAGE;                // per warp
+    // dC of the current row held in registers (at most two float4 per lane);
+    // wider shapes stage and read dC for every nonzero
+    static constexpr bool ROW_DC = K::VPL * DV <= 2;
     static_assert(SPB == 1 || K::IPL == 1, "split batches need one item per lane");
 };
 
@@ -87,9 +93,11 @@ __device__ __forceinline__ void sddmm_walk(const SddmmProblem& sp, int i, int cs
         int col[IPL];
         int e[IPL];
         uint32_t ends, nz;
+        uint32_t rs;     // bit t: item t is the first nonzero of its row in this walk
         int rbase;
     };
     int beta = 0, ecur = y0, r = x0;
+    uint32_t prev_end = 1u;   // the item before the next batch ends a row (or the walk starts)
     auto decode = [&](Batch& B) {
         uint32_t m = 0;
 #pragma unroll
@@ -117,6 +125,8 @@ __device__ __forceinline__ void sddmm_walk(const SddmmProblem& sp, int i, int cs
         }
         B.ends = m;
         B.nz = nz;
+        B.rs = nz & ((m << 1) | prev_end);
+        prev_end = (m >> (MB - 1)) & 1u;
         B.rbase = r;
         r += __popc(m);
         ecur += __popc(nz);
@@ -155,20 +165,30 @@ __device__ __forceinline__ void sddmm_walk(const SddmmProblem& sp, int i, int cs
             }
             const bool live = (X.nz >> tt) & 1u;
             const int ok = live ? 16 : 0;
-            const int row = X.rbase + __popc(X.ends & ((1u << tt) - 1u));
             const char* rp = brow(lc, cc);
-            const float* dr = sp.dC + (int64_t)(live ? row : 0) * sp.lddc;
 #pragma unroll
-            for (int q = 0; q < VPL; ++q) {
+            for (int q = 0; q < VPL; ++q)
                 cp_async16(buf + (uint32_t)((s * S::SLOTS + q) * 512), rp + lc.qoff[q], ok);
+            if (S::ROW_DC ? ((X.rs >> tt) & 1u) : live) {
+                // (first) nonzero of its row: stage the row's dC segment
+                const int row = X.rbase + __popc(X.ends & ((1u << tt) - 1u));
+                const float* dr = sp.dC + (int64_t)row * sp.lddc;
 #pragma unroll
-                for (int k = 0; k < DV; ++k)
-                    cp_async16(buf + (uint32_t)((s * S::SLOTS + VPL + q * DV + k) * 512),
-                               dr + dcoff[q] + k * 4, ((lc.vmask >> q) & 1u) ? ok : 0);
+                for (int q = 0; q < VPL; ++q)
+#pragma unroll
+                    for (int k = 0; k < DV; ++k)
+                        cp_async16(buf + (uint32_t)((s * S::SLOTS + VPL + q * DV + k) * 512),
+                                   dr + dcoff[q] + k * 4, ((lc.vmask >> q) & 1u) ? 16 : 0);
             }
         }
         cp_async_commit();
     };
+
+    // this lane's columns of the current row of dC, loaded from the stage
+    // slot of the row's first nonzero
+    uint4 dcur[S::ROW_DC ? VPL * DV : 1];
+#pragma unroll
+    for (int k = 0; k < (S::ROW_DC ? VPL * DV : 1); ++k) dcur[k] = make_uint4(0u, 0u, 0u, 0u);
 
     // per-lane partial dot product of item s of the stage
     auto partial = [&](uint32_t buf, int s) -> float {
@@ -187,7 +207,9 @@ __device__ __forceinline__ void sddmm_walk(const SddmmProblem& sp, int i, int cs
             }
 #pragma unroll
             for (int k = 0; k < DV; ++k) {
-                const uint4 dv = lds128(buf + (uint32_t)((s * S::SLOTS + VPL + q * DV + k) * 512));
+                const uint4 dv =
+                    S::ROW_DC ? dcur[q * DV + k]
+                              : lds128(buf + (uint32_t)((s * S::SLOTS + VPL + q * DV + k) * 512));
                 a = fmaf(__uint_as_float(dv.x), bf[4 * k + 0], a);
                 b = fmaf(__uint_as_float(dv.y), bf[4 * k + 1], b);
                 a = fmaf(__uint_as_float(dv.z), bf[4 * k + 2], a);
@@ -201,7 +223,17 @@ __device__ __forceinline__ void sddmm_walk(const SddmmProblem& sp, int i, int cs
         const uint32_t buf = wbase + lane * 16 + (uint32_t)(t & 1) * S::STAGE;
         float v[SS];
 #pragma unroll
-        for (int s = 0; s < SS; ++s) v[s] = partial(buf, s);
+        for (int s = 0; s < SS; ++s) {
+            const int tt = (SPB == 1 ? 0 : h * SS) + s;
+            if constexpr (S::ROW_DC) {
+                if ((X.rs >> tt) & 1u) {
+#pragma unroll
+                    for (int k = 0; k < VPL * DV; ++k)
+                        dcur[k] = lds128(buf + (uint32_t)((s * S::SLOTS + VPL + k) * 512));
+                }
+            }
+            v[s] = partial(buf, s);
+        }
         if constexpr (SS <= LPN) {
             // plain halves while the group is wider than the stage ...
 #pragma unroll

@@ -82,12 +82,20 @@ def test_dB_through_transpose(sym):
     assert_close_rel(dB.numpy(), ref, bound, TOL_F32, "dB = A^T dC")
 
 
-@pytest.mark.parametrize("N", [16, 64, 128])
+@pytest.mark.parametrize("N,bdtype", [(8, torch.float32), (16, torch.float32),
+                                       (32, torch.float32), (64, torch.float32),
+                                       (128, torch.float32), (256, torch.float32),
+                                       (512, torch.float32), (16, torch.bfloat16),
+                                       (64, torch.bfloat16), (256, torch.bfloat16),
+                                       (512, torch.bfloat16)])
 @pytest.mark.parametrize("use_plan", [False, True])
-def test_sddmm(N, use_plan):
+def test_sddmm(N, bdtype, use_plan):
+    """Every lane shape (2 to 32 lanes, 1 to 4 vectors per lane), with the dC
+    row held in registers (narrow shapes) or staged per nonzero (wide ones),
+    FP32 and BF16 B, against the FP64 oracle on the stored inputs."""
     A = inputs.rmat_csr(12, 16, seed=48)
     dC = inputs.dense_normal(A.M, N, seed=49)
-    B = inputs.dense_normal(A.K, N, seed=50)
+    B = inputs.dense_normal(A.K, N, seed=50).to(bdtype)
     Ad = A.to("cuda")
     out = torch.full((A.nnz,), float("nan"), device="cuda")
     if use_plan:
@@ -101,9 +109,12 @@ def test_sddmm(N, use_plan):
                            plan=plan, ws=ws)
     torch.cuda.synchronize()
     assert binding.spmm_get_device_status(ws) == 0
-    ref = oracle.sddmm(A.rowptr, A.colind, dC, B)
-    bound = oracle.sddmm(A.rowptr, A.colind, np.abs(dC.numpy().astype(np.float64)),
-                         np.abs(B.numpy().astype(np.float64)))
-    assert_close_rel(out.cpu().numpy(), ref, bound, TOL_F32, f"sddmm N={N}")
+    if bdtype == torch.bfloat16:
+        B64 = oracle.decode_bf16(B.view(torch.int16).numpy().view(np.uint16))
+    else:
+        B64 = B.numpy().astype(np.float64)
+    ref = oracle.sddmm(A.rowptr, A.colind, dC, B64)
+    bound = oracle.sddmm(A.rowptr, A.colind, np.abs(dC.numpy().astype(np.float64)), np.abs(B64))
+    assert_close_rel(out.cpu().numpy(), ref, bound, TOL_F32, f"sddmm N={N} {bdtype}")
     if plan is not None:
         plan.close()
