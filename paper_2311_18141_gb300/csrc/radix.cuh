@@ -8,16 +8,16 @@
 
 namespace spmm {
 
-// Scratch (bytes) of radix_sort_pairs / scan_exclusive_i32 for n elements; the
-// caller provides it 256-byte aligned.
-size_t radix_scratch_bytes(int64_t n);
+// Scratch (bytes) of radix_sort_pairs for n keys of key_bits bits, and of
+// scan_exclusive_i32 for n elements; the caller provides it 256-byte aligned.
+size_t radix_scratch_bytes(int64_t n, int key_bits);
 size_t scan_scratch_bytes(int64_t n);
 
 // Stable sort of n keys (key_bits significant bits; keys >= 0 and < 2^key_bits)
 // carrying a payload (vals == nullptr: the payload is the element's index).
-// The passes (8-bit digits) ping-pong between (k0, v0) and (k1, v1), which
-// must not alias the inputs; *out is set to 0 or 1, the pair that holds the
-// result.  Enqueued on s.
+// The passes -- the fewest of at most 9-bit digits, each digit at least 8
+// bits -- ping-pong between (k0, v0) and (k1, v1), which must not alias the
+// inputs; *out is set to 0 or 1, the pair that holds the result.  Enqueued on s.
 cudaError_t radix_sort_pairs(const int32_t* keys, const int32_t* vals, int64_t n, int key_bits,
                              int32_t* k0, int32_t* v0, int32_t* k1, int32_t* v1, void* scratch,
                              int* out, cudaStream_t s);

@@ -209,7 +209,9 @@ struct SpgemmLayout {
         crow, ccol, cval, total;
 };
 
-SpgemmLayout spgemm_layout(int64_t nnzA, int64_t P) {
+// The radix scratch comes last: its size depends on the key widths (bits of M
+// and N), the offsets of the output arrays do not.
+SpgemmLayout spgemm_layout(int64_t nnzA, int64_t P, int64_t M, int64_t N) {
     SpgemmLayout L;
     const size_t a = up256(4 * (size_t)(nnzA > 0 ? nnzA : 1));
     const size_t b = up256(4 * (size_t)(P > 0 ? P : 1));
@@ -227,13 +229,18 @@ SpgemmLayout spgemm_layout(int64_t nnzA, int64_t P) {
     L.rkey = o; o += b;
     L.icopy = o; o += b;
     L.pos = o; o += up256(4 * (size_t)(P + 1));
-    L.radix = o;
-    const size_t rs = radix_scratch_bytes(P);
-    const size_t ss = scan_scratch_bytes(P + 1);
-    o += rs > ss ? rs : ss;
     L.crow = o; o += b;
     L.ccol = o; o += b;
     L.cval = o; o += b;
+    L.radix = o;
+    const int bM = bits_for(M), bN = bits_for(N);
+    size_t rs = radix_scratch_bytes(P, bM + bN <= 32 ? bM + bN : bM);
+    if (bM + bN > 32) {
+        const size_t r2 = radix_scratch_bytes(P, bN);
+        if (r2 > rs) rs = r2;
+    }
+    const size_t ss = scan_scratch_bytes(P + 1);
+    o += rs > ss ? rs : ss;
     L.total = o;
     return L;
 }
@@ -291,7 +298,7 @@ extern "C" int spmm_spgemm_analyze(const int32_t* A_rowptr, const int32_t* A_col
     }
     if (P >= ((int64_t)1 << 31) - 1) return SPMM_ERR_UNSUPPORTED;   // products index in int32
     *products = P;
-    *workspace_bytes = spgemm_layout(nnzA, P).total;
+    *workspace_bytes = spgemm_layout(nnzA, P, M, N).total;
     return SPMM_OK;
 }
 
@@ -306,7 +313,7 @@ extern "C" int spmm_spgemm(const int32_t* A_rowptr, const int32_t* A_colind, con
     if (nnzA > 0 && !A_vals) return SPMM_ERR_INVALID_ARG;
     if (products > 0 && (!B_colind || !B_vals)) return SPMM_ERR_INVALID_ARG;
     const int64_t P = products;
-    const SpgemmLayout L = spgemm_layout(nnzA, P);
+    const SpgemmLayout L = spgemm_layout(nnzA, P, M, N);
     if (!workspace || workspace_bytes < L.total || ((uintptr_t)workspace & 255u))
         return SPMM_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
@@ -387,7 +394,7 @@ extern "C" int spmm_spgemm_copy(const void* workspace, int64_t M, int64_t nnzA, 
     if (entries > 0 && (!C_colind || !C_vals)) return SPMM_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const char* ws = static_cast<const char*>(workspace);
-    const SpgemmLayout L = spgemm_layout(nnzA, products);
+    const SpgemmLayout L = spgemm_layout(nnzA, products, 1, 1);   // output offsets only
     const int32_t* crow = reinterpret_cast<const int32_t*>(ws + L.crow);
     if (entries == 0) {
         if (cudaMemsetAsync(C_rowptr, 0, 4 * (size_t)(M + 1), s) != cudaSuccess) return SPMM_ERR_CUDA;

@@ -20,7 +20,8 @@ namespace spmm {
 constexpr int kSortThreads = 256;
 constexpr int kSortItems = 16;                         // keys per thread per tile
 constexpr int kTile = kSortThreads * kSortItems;       // 4096 keys per tile
-constexpr int kRadix = 256;
+constexpr int kMaxDigitBits = 9;   // digits of 8 or 9 bits: wider digits leave runs of 2-4 keys per
+                                   // digit and tile, whose scattered stores cost more than a pass
 constexpr int kScanBlock = 1024;                       // scan: elements per block-thread group
 
 int device_sm_count();
@@ -36,10 +37,13 @@ __global__ void expand_rows_kernel(const int32_t* __restrict__ rowptr, int64_t M
     }
 }
 
-// counts[d * ntiles + tile] = number of keys of the tile with digit d.
+// counts[d * ntiles + tile] = number of keys of the tile with digit d (digits of
+// DB bits).
+template <int DB>
 __global__ void __launch_bounds__(kSortThreads)
 radix_count_kernel(const int32_t* __restrict__ keys, int64_t n, int shift, int64_t ntiles,
                    int32_t* __restrict__ counts) {
+    constexpr int kRadix = 1 << DB;
     __shared__ int32_t h[kRadix];
     for (int d = threadIdx.x; d < kRadix; d += kSortThreads) h[d] = 0;
     __syncthreads();
@@ -54,7 +58,7 @@ radix_count_kernel(const int32_t* __restrict__ keys, int64_t n, int shift, int64
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k)
         if (base + (int64_t)k * kSortThreads + threadIdx.x < n)
-            atomicAdd(&h[((uint32_t)rkey[k] >> shift) & 0xff], 1);
+            atomicAdd(&h[((uint32_t)rkey[k] >> shift) & (kRadix - 1)], 1);
     __syncthreads();
     for (int d = threadIdx.x; d < kRadix; d += kSortThreads) counts[(int64_t)d * ntiles + tile] = h[d];
 }
@@ -152,17 +156,27 @@ scan_apply_kernel(int32_t* __restrict__ data, int64_t n, int64_t per_block,
 // are then placed in shared memory at (tile-local start of the digit) +
 // (earlier warps' count of the digit) + (rank): (digit, index) order, stable.
 // The tile is written out in that order, so each digit's keys leave as one
-// contiguous run at the digit's global offset (coalesced stores).
-__global__ void __launch_bounds__(kSortThreads)
+// contiguous run at the digit's global offset (coalesced stores).  Digits of DB
+// bits; the digit tables live in dynamic shared memory (scatter_smem_bytes(DB)),
+// the staged keys and payloads in static shared memory.
+constexpr size_t scatter_smem_bytes(int db) {
+    return 4 * (size_t)(kSortThreads / 32 + 3) * ((size_t)1 << db);
+}
+
+template <int DB>
+__global__ void __launch_bounds__(kSortThreads, 2)
 radix_scatter_kernel(const int32_t* __restrict__ keys_in, const int32_t* __restrict__ vals_in,
                      int64_t n, int shift, int64_t ntiles, const int32_t* __restrict__ offsets,
                      int32_t* __restrict__ keys_out, int32_t* __restrict__ vals_out) {
+    constexpr int kRadix = 1 << DB;
     constexpr int W = kSortThreads / 32;
     constexpr int KW = 32 * kSortItems;     // keys per warp
-    __shared__ int32_t wc[W][kRadix];       // per-warp digit counts, then per-warp offsets
-    __shared__ int32_t tot[kRadix];         // tile digit counts
-    __shared__ int32_t lstart[kRadix];      // tile-local start of each digit
-    __shared__ int32_t gdelta[kRadix];      // global offset - local start, per digit
+    extern __shared__ int32_t radix_smem[];
+    // per-warp digit counts, then per-warp offsets
+    int32_t(*__restrict__ wc)[kRadix] = reinterpret_cast<int32_t(*)[kRadix]>(radix_smem);
+    int32_t* __restrict__ tot = radix_smem + W * kRadix;   // tile digit counts
+    int32_t* __restrict__ lstart = tot + kRadix;           // tile-local start of each digit
+    int32_t* __restrict__ gdelta = lstart + kRadix;        // global offset - local start
     __shared__ int32_t skey[kTile];
     __shared__ int32_t sval[kTile];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -182,7 +196,7 @@ radix_scatter_kernel(const int32_t* __restrict__ keys_in, const int32_t* __restr
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
         const bool ok = warp * KW + k * 32 + lane < cnt;
-        const int d = ok ? (int)(((uint32_t)rkey[k] >> shift) & 0xff) : kRadix;   // kRadix = none
+        const int d = ok ? (int)(((uint32_t)rkey[k] >> shift) & (kRadix - 1)) : kRadix;   // kRadix = none
         const unsigned peers = __match_any_sync(kFull, d);
         const int r = __popc(peers & ((1u << lane) - 1u));
         const int32_t before = ok ? wc[warp][d] : 0;
@@ -223,7 +237,7 @@ radix_scatter_kernel(const int32_t* __restrict__ keys_in, const int32_t* __restr
 #pragma unroll
     for (int k = 0; k < kSortItems; ++k) {
         if (warp * KW + k * 32 + lane < cnt) {
-            const int d = (int)(((uint32_t)rkey[k] >> shift) & 0xff);
+            const int d = (int)(((uint32_t)rkey[k] >> shift) & (kRadix - 1));
             const int32_t lp = lstart[d] + wc[warp][d] + rr[k];
             skey[lp] = rkey[k];
             sval[lp] = rval[k];
@@ -233,7 +247,7 @@ radix_scatter_kernel(const int32_t* __restrict__ keys_in, const int32_t* __restr
     // write out in (digit, index) order: runs of equal digits are contiguous
     for (int lp = threadIdx.x; lp < cnt; lp += kSortThreads) {
         const int32_t key = skey[lp];
-        const int d = (int)(((uint32_t)key >> shift) & 0xff);
+        const int d = (int)(((uint32_t)key >> shift) & (kRadix - 1));
         const int64_t pos = (int64_t)gdelta[d] + lp;
         keys_out[pos] = key;
         vals_out[pos] = sval[lp];
@@ -302,11 +316,42 @@ cudaError_t scan_exclusive_i32(int32_t* data, int64_t n, void* scratch, cudaStre
     return cudaGetLastError();
 }
 
-// Radix scratch: the digit-major count table (256 x tiles) and its scan sums.
-size_t radix_scratch_bytes(int64_t n) {
+// Passes and digit width for keys of key_bits bits: the fewest passes of at
+// most kMaxDigitBits bits, each digit as narrow as that allows but at least 8.
+static void radix_digits(int key_bits, int* passes, int* width) {
+    int p = (key_bits + kMaxDigitBits - 1) / kMaxDigitBits;
+    if (p < 1) p = 1;
+    int w = (key_bits + p - 1) / p;
+    if (w < 8) w = 8;
+    *passes = p;
+    *width = w;
+}
+
+// Radix scratch: the digit-major count table (buckets x tiles) and its scan sums.
+size_t radix_scratch_bytes(int64_t n, int key_bits) {
+    int passes = 0, width = 0;
+    radix_digits(key_bits, &passes, &width);
     const int64_t ntiles = n > 0 ? (n + kTile - 1) / kTile : 1;
-    const int64_t ncounts = ntiles * kRadix;
+    const int64_t ncounts = ntiles << width;
     return up256(4 * (size_t)ncounts) + scan_scratch_bytes(ncounts);
+}
+
+// One pass over digits of DB bits at `shift`: count, scan, scatter.
+template <int DB>
+static cudaError_t radix_pass(const int32_t* kin, const int32_t* vin, int64_t n, int shift,
+                              int64_t ntiles, int32_t* counts, void* sums, int32_t* kout,
+                              int32_t* vout, cudaStream_t s) {
+    const int64_t ncounts = ntiles << DB;
+    const size_t smem = scatter_smem_bytes(DB);
+    cudaError_t e = cudaFuncSetAttribute(radix_scatter_kernel<DB>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    radix_count_kernel<DB><<<(unsigned)ntiles, kSortThreads, 0, s>>>(kin, n, shift, ntiles, counts);
+    e = scan_exclusive_i32(counts, ncounts, sums, s);
+    if (e != cudaSuccess) return e;
+    radix_scatter_kernel<DB><<<(unsigned)ntiles, kSortThreads, smem, s>>>(kin, vin, n, shift, ntiles,
+                                                                          counts, kout, vout);
+    return cudaGetLastError();
 }
 
 cudaError_t radix_sort_pairs(const int32_t* keys, const int32_t* vals, int64_t n, int key_bits,
@@ -314,23 +359,25 @@ cudaError_t radix_sort_pairs(const int32_t* keys, const int32_t* vals, int64_t n
                              int* out, cudaStream_t s) {
     *out = 0;
     if (n <= 0) return cudaSuccess;
+    int passes = 0, width = 0;
+    radix_digits(key_bits, &passes, &width);
     const int64_t ntiles = (n + kTile - 1) / kTile;
-    const int64_t ncounts = ntiles * kRadix;
+    const int64_t ncounts = ntiles << width;
     int32_t* counts = static_cast<int32_t*>(scratch);
     void* sums = static_cast<char*>(scratch) + up256(4 * (size_t)ncounts);
     int32_t* kb[2] = {k0, k1};
     int32_t* vb[2] = {v0, v1};
     const int32_t* kin = keys;
     const int32_t* vin = vals;   // nullptr: first pass carries the index
-    const int passes = (key_bits + 7) / 8 > 0 ? (key_bits + 7) / 8 : 1;
     int cur = 0;
     for (int pass = 0; pass < passes; ++pass) {
-        const int shift = 8 * pass;
-        radix_count_kernel<<<(unsigned)ntiles, kSortThreads, 0, s>>>(kin, n, shift, ntiles, counts);
-        cudaError_t e = scan_exclusive_i32(counts, ncounts, sums, s);
+        const int shift = width * pass;
+        cudaError_t e;
+        if (width == 8)
+            e = radix_pass<8>(kin, vin, n, shift, ntiles, counts, sums, kb[cur], vb[cur], s);
+        else
+            e = radix_pass<9>(kin, vin, n, shift, ntiles, counts, sums, kb[cur], vb[cur], s);
         if (e != cudaSuccess) return e;
-        radix_scatter_kernel<<<(unsigned)ntiles, kSortThreads, 0, s>>>(kin, vin, n, shift, ntiles,
-                                                                       counts, kb[cur], vb[cur]);
         kin = kb[cur];
         vin = vb[cur];
         *out = cur;
@@ -361,7 +408,7 @@ struct TransposeLayout {
     size_t row_of, keys0, keys1, vals0, vals1, scratch, total;
 };
 
-static TransposeLayout transpose_layout(int64_t nnz) {
+static TransposeLayout transpose_layout(int64_t nnz, int64_t K) {
     TransposeLayout L;
     size_t off = 0;
     const size_t a = up256(4 * (size_t)(nnz > 0 ? nnz : 1));
@@ -370,7 +417,7 @@ static TransposeLayout transpose_layout(int64_t nnz) {
     L.keys1 = off; off += a;
     L.vals0 = off; off += a;
     L.vals1 = off; off += a;
-    L.scratch = off; off += radix_scratch_bytes(nnz);
+    L.scratch = off; off += radix_scratch_bytes(nnz, bits_for(K));
     L.total = off;
     return L;
 }
@@ -382,7 +429,7 @@ using namespace spmm;
 extern "C" int spmm_csr_transpose_workspace_size(int64_t M, int64_t K, int64_t nnz,
                                                  size_t* bytes) {
     if (!bytes || M < 0 || K < 0 || nnz < 0) return SPMM_ERR_INVALID_ARG;
-    *bytes = transpose_layout(nnz).total;
+    *bytes = transpose_layout(nnz, K).total;
     return SPMM_OK;
 }
 
@@ -397,7 +444,7 @@ extern "C" int spmm_csr_transpose(const int32_t* A_rowptr, const int32_t* A_coli
         return SPMM_ERR_INVALID_ARG;
     if (out_vals && elem_bytes(val_dtype) == 0) return SPMM_ERR_UNSUPPORTED;
     if (nnz > 0 && out_vals && !A_vals) return SPMM_ERR_INVALID_ARG;
-    const TransposeLayout L = transpose_layout(nnz);
+    const TransposeLayout L = transpose_layout(nnz, K);
     if (!workspace || workspace_bytes < L.total || ((uintptr_t)workspace & 255u))
         return SPMM_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
