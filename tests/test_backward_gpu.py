@@ -29,7 +29,12 @@ def transpose_gpu(A, with_vals=True):
             perm.cpu()[:n])
 
 
-@pytest.mark.parametrize("shape", [("rmat", 12), ("rmat", 15), ("uniform", 0), ("gcn", 12)])
+# column keys of 12, 15, 17, 9, 21 and 26 bits: two 8-bit passes, two 9-bit
+# passes, one 9-bit pass, three 8-bit passes and three 9-bit passes
+@pytest.mark.parametrize("shape", [("rmat", 12), ("rmat", 15), ("uniform", (3000, 70000, 9)),
+                                   ("gcn", 12), ("uniform", (2000, 300, 7)),
+                                   ("uniform", (1500, (1 << 20) + 77, 4)),
+                                   ("uniform", (1200, (1 << 25) + 12345, 5))])
 def test_transpose_bit_exact(shape):
     kind, s = shape
     if kind == "rmat":
@@ -37,7 +42,8 @@ def test_transpose_bit_exact(shape):
     elif kind == "gcn":
         A = inputs.gcn_normalized_adjacency(s, 16, seed=42)
     else:
-        A = inputs.uniform_csr(3000, 70000, 9, seed=43)   # K needs 3 radix passes
+        M, K, per_row = s
+        A = inputs.uniform_csr(M, K, per_row, seed=43)
     colptr, rowind, tv, perm = transpose_gpu(A)
     c_ref, r_ref, v_ref, p_ref = oracle.csr_transpose(A.rowptr, A.colind, A.vals, A.K)
     np.testing.assert_array_equal(colptr.numpy(), c_ref)
