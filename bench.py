@@ -26,6 +26,8 @@ import subprocess
 import sys
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -197,42 +199,57 @@ def tile_nnz_imbalance(rowptr, M: int, TR: int) -> float:
     return max(per) / avg if avg > 0 else 1.0
 
 
-def cpu_oracle_sample(A, B, seconds: float):
-    """Time the FP64 oracle on a stride sample of rows, growing it until about
-    `seconds` of CPU work; returns (GFLOP/s, cores, description)."""
-    import numpy as np
+def _host_operands(A, B):
+    """A's CSR arrays and B as host numpy arrays (copied once)."""
+    return (A.rowptr.cpu().numpy(), A.colind.cpu().numpy(), A.vals.cpu().numpy(),
+            B.cpu().numpy())
+
+
+def _oracle_stride(host, M: int, seconds: float) -> int:
+    """Row stride whose oracle sample takes about `seconds` (at least a quarter
+    of it), found by growing the sample 4x at a time; 1 = every row."""
     import oracle
-    cores = len(os.sched_getaffinity(0))
-    oracle.set_threads(cores)
-    rp = A.rowptr.cpu().numpy()
-    ci = A.colind.cpu().numpy()
-    v = A.vals.cpu().numpy()
-    Bh = B.cpu().numpy()
-    N = Bh.shape[1]
-    lens = np.diff(rp.astype(np.int64))
+    rp, ci, v, Bh = host
     stride = 4096
-    total_t, total_flops, rows_done = 0.0, 0.0, 0
-    while stride >= 1:
-        rows = np.arange(0, A.M, stride, dtype=np.int64)
+    while stride > 1:
+        rows = np.arange(0, M, stride, dtype=np.int64)
         t = time.perf_counter()
         oracle.spmm_rows(rp, ci, v, Bh, rows)
-        dt = time.perf_counter() - t
-        total_t, total_flops, rows_done = dt, 2.0 * float(lens[rows].sum()) * N, rows.size
-        if dt >= seconds / 4 or stride == 1:
+        if time.perf_counter() - t >= seconds / 4:
             break
         stride //= 4
-    # a whole pass that is still short is repeated until the time budget is used
-    reps = 1
-    while stride == 1 and total_t < seconds:
+    return max(stride, 1)
+
+
+def _oracle_timed(host, M: int, stride: int, seconds: float):
+    """One timed oracle sample at `stride` (whole passes repeated while a
+    stride-1 pass is shorter than `seconds`): (GFLOP/s, threads, description,
+    seconds spent)."""
+    import oracle
+    rp, ci, v, Bh = host
+    N = Bh.shape[1]
+    lens = np.diff(rp.astype(np.int64))
+    rows = np.arange(0, M, stride, dtype=np.int64)
+    flops = 2.0 * float(lens[rows].sum()) * N
+    total_t, reps = 0.0, 0
+    while reps == 0 or (stride == 1 and total_t < seconds):
         t = time.perf_counter()
         oracle.spmm_rows(rp, ci, v, Bh, rows)
         total_t += time.perf_counter() - t
         reps += 1
-    total_flops *= reps
-    desc = (f"every {stride}-th row of the workload ({rows_done} rows, "
-            f"{total_flops / reps / 2 / N:.0f} nnz) x {reps} pass(es), N={N}, FP64 oracle, "
+    desc = (f"every {stride}-th row of the workload ({rows.size} rows, "
+            f"{flops / 2 / N:.0f} nnz) x {reps} pass(es), N={N}, FP64 oracle, "
             f"{total_t:.2f} s")
-    return total_flops / total_t / 1e9, oracle.get_threads(), desc, total_t
+    return flops * reps / total_t / 1e9, oracle.get_threads(), desc, total_t
+
+
+def cpu_oracle_sample(A, B, seconds: float):
+    """Time the FP64 oracle on a stride sample of rows of about `seconds` of CPU
+    work; returns (GFLOP/s, threads, description, seconds spent)."""
+    import oracle
+    oracle.set_threads(len(os.sched_getaffinity(0)))
+    host = _host_operands(A, B)
+    return _oracle_timed(host, A.M, _oracle_stride(host, A.M, seconds), seconds)
 
 
 def job_throughput(local_total_ms: float, steps: int, flops_per_step: float, world: int,
@@ -261,14 +278,19 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    import oracle
     A, B = make_workload(args.scale, args.n, "cuda" if torch.cuda.is_available() else "cpu")
+    oracle.set_threads(len(os.sched_getaffinity(0)))
+    host = _host_operands(A, B)
+    # every step is one bounded sample, sized so the whole run takes about two minutes
+    per_step = max(0.02, min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup)))
+    stride = _oracle_stride(host, A.M, per_step)
     vals = []
-    per_step = max(0.5, min(args.cpu_seconds, 120.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
-        cpu_oracle_sample(A, B, per_step)
+        _oracle_timed(host, A.M, stride, per_step)
     desc = cores = None
     for _ in range(args.steps):
-        g, cores, desc, _ = cpu_oracle_sample(A, B, per_step)
+        g, cores, desc, _ = _oracle_timed(host, A.M, stride, per_step)
         vals.append(g)
     value = sum(vals) / len(vals)
     flops_step = 2.0 * A.nnz * args.n
