@@ -306,6 +306,18 @@ int spmm_spgemm_copy(const void* workspace, int64_t M, int64_t nnzA, int64_t pro
 int spmm_get_device_status(void* workspace, int32_t* status, void* stream);
 
 /*
+ * spmm_selftest_wait_timeout -- exercise the bounded device wait.  One thread
+ *   waits on an mbarrier phase that nothing completes, for at most
+ *   limit_cycles SM cycles (1 .. 2^31; 2^20 is about half a millisecond),
+ *   then writes SPMM_ERR_TIMEOUT into the status word of `workspace` (device,
+ *   at least 64 bytes) and returns; the CUDA context stays usable.  This is
+ *   how a product reports copies that never arrive, without faulting or
+ *   hanging the GPU.  Read the result with spmm_get_device_status.
+ */
+int spmm_selftest_wait_timeout(void* workspace, size_t workspace_bytes, int64_t limit_cycles,
+                               void* stream);
+
+/*
  * Host-buffer pipeline -- the local product C = A B of Section 2.1 for
  * operands that live in host memory, one product per submitted step.  Each
  * step copies A (rowptr, colind, vals) and B from the host to the device,

@@ -39,7 +39,7 @@ EXPORTED = [
     "spmm_batch_set_shapes", "spmm_batch_get_shapes", "spmm_csr_batched",
     "spmm_batch_graph_launch", "spmm_batch_autotune", "spmm_spgemm_analyze", "spmm_spgemm",
     "spmm_spgemm_copy", "spmm_host_pipe_create", "spmm_host_pipe_submit", "spmm_host_pipe_wait",
-    "spmm_host_pipe_destroy",
+    "spmm_host_pipe_destroy", "spmm_selftest_wait_timeout",
 ]
 
 
@@ -116,6 +116,7 @@ def load_library(path: str | None = None):
         lib.spmm_csr_batched.argtypes = [vp, vp, sz, vp]
         lib.spmm_batch_graph_launch.argtypes = [vp, vp, sz, vp]
         lib.spmm_batch_autotune.argtypes = [vp, vp, sz, i32, vp, P(ctypes.c_float)]
+        lib.spmm_selftest_wait_timeout.argtypes = [vp, sz, i64, vp]
         lib.spmm_host_pipe_create.argtypes = [P(vp), vp, i32, i32, i32, vp]
         lib.spmm_host_pipe_submit.argtypes = [vp, vp, vp, vp, vp, vp]
         lib.spmm_host_pipe_wait.argtypes = [vp]
@@ -284,6 +285,14 @@ def spmm_csr_noalloc(rowptr, colind, vals, B, C, M, K, N, nnz, *, a_scale=None, 
         dtype_code(B.dtype), _ptr(b_scale), int(B.stride(0)), _ptr(C), int(C.stride(0)), int(M),
         int(K), int(N), int(nnz), int(tile_rows), int(tile_cols), float(beta), _stream(stream)),
         "spmm_csr_noalloc")
+
+
+def spmm_selftest_wait_timeout(ws, limit_cycles: int = 1 << 20, stream=None) -> None:
+    """Run the bounded-wait self-test; the status word of ``ws`` then holds
+    SPMM_ERR_TIMEOUT (read it with spmm_get_device_status)."""
+    _check(load_library().spmm_selftest_wait_timeout(_ptr(ws), ws.numel() * ws.element_size(),
+                                                     int(limit_cycles), _stream(stream)),
+           "spmm_selftest_wait_timeout")
 
 
 def spmm_csr_validate(rowptr, colind, M, K, nnz, ws, stream=None) -> None:

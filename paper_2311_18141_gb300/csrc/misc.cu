@@ -76,6 +76,24 @@ __global__ void gather_kernel(const T* __restrict__ in, const int32_t* __restric
         out[i] = in[perm[i]];
 }
 
+// Bounded-wait self-test.  One thread initialises an mbarrier that expects one
+// arrival, never arrives on it, and waits on its first phase for at most
+// `limit` SM cycles -- the wait the bulk-copy staging does for its copies.
+// When the wait runs out it records SPMM_ERR_TIMEOUT in the status word, the
+// way a kernel whose copies never land reports it and returns.
+__global__ void wait_timeout_selftest_kernel(int32_t* status, long long limit) {
+    __shared__ __align__(8) unsigned long long bar_mem;
+    if (threadIdx.x != 0) return;
+    const uint32_t bar = (uint32_t)__cvta_generic_to_shared(&bar_mem);
+    mbar_init(bar, 1);
+    mbar_init_fence();
+    bool done = mbar_try_wait(bar, 0);
+    const long long t0 = clock64();
+    while (!done && clock64() - t0 <= limit) done = mbar_try_wait(bar, 0);
+    if (!done) atomicCAS(status, 0, SPMM_ERR_TIMEOUT);
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" :: "r"(bar) : "memory");
+}
+
 int device_sm_count();
 
 static unsigned grid_for(int64_t work, int threads) {
@@ -111,6 +129,15 @@ int spmm_quantize_rows(const float* X, int64_t rows, int64_t cols, int64_t ldx, 
     const int threads = 256;
     quantize_rows_kernel<<<grid_for(rows * 32, threads), threads, 0, s>>>(X, rows, cols, ldx, dtype,
                                                                          Xq, ldq, scale);
+    return cudaGetLastError() == cudaSuccess ? SPMM_OK : SPMM_ERR_CUDA;
+}
+
+int spmm_selftest_wait_timeout(void* workspace, size_t workspace_bytes, int64_t limit_cycles,
+                               void* stream) {
+    if (!workspace || workspace_bytes < kStatusBytes) return SPMM_ERR_WORKSPACE;
+    if (limit_cycles < 1 || limit_cycles > ((int64_t)1 << 31)) return SPMM_ERR_INVALID_ARG;
+    wait_timeout_selftest_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(
+        static_cast<int32_t*>(workspace), (long long)limit_cycles);
     return cudaGetLastError() == cudaSuccess ? SPMM_OK : SPMM_ERR_CUDA;
 }
 
