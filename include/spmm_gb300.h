@@ -128,6 +128,31 @@ int spmm_plan_workspace_size(spmm_plan plan, size_t* bytes);
  * reporting. */
 int spmm_plan_units(spmm_plan plan, int64_t* chunks, int64_t* units);
 
+/*
+ * Per-warp trace of the persistent SpMM kernel: the on-chip counterpart of the
+ * paper's split of run time into computation and load imbalance (Section 6).
+ * Each warp of a spmm_csr launch with a traced plan writes one record, warp w
+ * (= blockIdx.x * warps_per_cta + warp in CTA) to records[w] when w <
+ * max_records; records past the launched warps are left untouched.
+ */
+typedef struct spmm_trace_record {
+    int64_t t_start_ns;   /* %globaltimer when the warp started               */
+    int64_t t_end_ns;     /* %globaltimer when it ran out of work             */
+    int32_t units;        /* work units (32/LPN chunks of one tile) it walked */
+    int32_t stolen;       /* of those, units outside its home tile (row)      */
+    int32_t home;         /* its home tile (or tile row, interleaved order)   */
+    int32_t smid;         /* the SM it ran on                                 */
+} spmm_trace_record;
+
+/*
+ * spmm_plan_set_trace -- make spmm_csr calls with `plan` write trace records
+ *   to `records` (device, spmm_trace_record[max_records], caller-owned; the
+ *   buffer must outlive those calls).  records == NULL or max_records == 0
+ *   turns tracing off.  A traced launch does the same work; each warp adds one
+ *   32-byte store at its end.
+ */
+int spmm_plan_set_trace(spmm_plan plan, spmm_trace_record* records, int32_t max_records);
+
 /* Bytes of workspace a spmm_csr call with plan == NULL needs: the plan arrays
  * plus the per-call scratch.  Such calls use the default tuning; `tuning` is
  * reserved and should be NULL. */

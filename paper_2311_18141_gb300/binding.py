@@ -12,6 +12,7 @@ import ctypes
 import os
 import threading
 
+import numpy as np
 import torch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
@@ -39,8 +40,12 @@ EXPORTED = [
     "spmm_batch_set_shapes", "spmm_batch_get_shapes", "spmm_csr_batched",
     "spmm_batch_graph_launch", "spmm_batch_autotune", "spmm_spgemm_analyze", "spmm_spgemm",
     "spmm_spgemm_copy", "spmm_host_pipe_create", "spmm_host_pipe_submit", "spmm_host_pipe_wait",
-    "spmm_host_pipe_destroy", "spmm_selftest_wait_timeout",
+    "spmm_host_pipe_destroy", "spmm_selftest_wait_timeout", "spmm_plan_set_trace",
 ]
+
+# spmm_trace_record: per-warp record of a traced spmm_csr launch
+TRACE_DTYPE = np.dtype([("t_start_ns", "<i8"), ("t_end_ns", "<i8"), ("units", "<i4"),
+                        ("stolen", "<i4"), ("home", "<i4"), ("smid", "<i4")])
 
 
 class SpmmError(RuntimeError):
@@ -117,6 +122,7 @@ def load_library(path: str | None = None):
         lib.spmm_batch_graph_launch.argtypes = [vp, vp, sz, vp]
         lib.spmm_batch_autotune.argtypes = [vp, vp, sz, i32, vp, P(ctypes.c_float)]
         lib.spmm_selftest_wait_timeout.argtypes = [vp, sz, i64, vp]
+        lib.spmm_plan_set_trace.argtypes = [vp, vp, i32]
         lib.spmm_host_pipe_create.argtypes = [P(vp), vp, i32, i32, i32, vp]
         lib.spmm_host_pipe_submit.argtypes = [vp, vp, vp, vp, vp, vp]
         lib.spmm_host_pipe_wait.argtypes = [vp]
@@ -170,6 +176,17 @@ def make_tuning(chunk_items=0, warps_per_cta=0, ctas_per_sm=0, tile_order=0) -> 
     return t
 
 
+def trace_buffer(records: int, device=None) -> torch.Tensor:
+    """Zeroed device buffer for ``records`` trace records."""
+    return torch.zeros(records * TRACE_DTYPE.itemsize, dtype=torch.uint8, device=device or "cuda")
+
+
+def read_trace(buf: torch.Tensor) -> np.ndarray:
+    """The records of a trace buffer that a launch wrote (t_end_ns > 0)."""
+    rec = buf.cpu().numpy().view(TRACE_DTYPE)
+    return rec[rec["t_end_ns"] > 0]
+
+
 def workspace(nbytes: int, device=None) -> torch.Tensor:
     """Device scratch of at least ``nbytes`` (256-byte aligned by the caching allocator)."""
     return torch.zeros(max(int(nbytes), 256), dtype=torch.uint8, device=device or "cuda")
@@ -193,6 +210,14 @@ class Plan:
         _check(lib.spmm_plan_workspace_size(self.handle, ctypes.byref(n)),
                "spmm_plan_workspace_size")
         self.workspace_bytes = int(n.value)
+
+    def set_trace(self, records: torch.Tensor | None) -> None:
+        """Trace later spmm_csr calls with this plan into ``records`` (a device
+        buffer from trace_buffer), or stop tracing (None)."""
+        n = 0 if records is None else records.numel() * records.element_size() // TRACE_DTYPE.itemsize
+        _check(load_library().spmm_plan_set_trace(self.handle, _ptr(records), int(n)),
+               "spmm_plan_set_trace")
+        self._trace = records   # the plan writes into it: keep it alive
 
     def units(self) -> tuple[int, int]:
         c, u = ctypes.c_int64(), ctypes.c_int64()

@@ -18,6 +18,8 @@ struct spmm_plan_s {
     int32_t* blk_base;
     int32_t* bnd_row;
     int32_t* bnd_nnz;
+    spmm_trace_record* trace;   // caller-owned per-warp trace records (null: off)
+    int32_t trace_max;
 };
 
 namespace spmm {
@@ -186,6 +188,13 @@ int spmm_plan_destroy(spmm_plan plan) {
     return SPMM_OK;
 }
 
+int spmm_plan_set_trace(spmm_plan plan, spmm_trace_record* records, int32_t max_records) {
+    if (!plan || max_records < 0) return SPMM_ERR_INVALID_ARG;
+    plan->trace = max_records > 0 ? records : nullptr;
+    plan->trace_max = plan->trace ? max_records : 0;
+    return SPMM_OK;
+}
+
 int spmm_plan_workspace_size(spmm_plan plan, size_t* bytes) {
     if (!plan || !bytes) return SPMM_ERR_INVALID_ARG;
     *bytes = scratch_layout(plan->TR, plan->TC, plan->cap, plan->N).total;
@@ -287,6 +296,10 @@ int spmm_csr(const int32_t* A_rowptr, const int32_t* A_colind, const void* A_val
     p.tile_ctr = reinterpret_cast<int32_t*>(ws + sc.counters_off);
     p.piece_cnt = p.tile_ctr + (size_t)TR * TC;
     p.slots = reinterpret_cast<float*>(ws + sc.slots_off);
+    if (plan) {
+        p.trace = plan->trace;
+        p.trace_max = plan->trace_max;
+    }
     if (cudaMemsetAsync(ws + sc.counters_off, 0, sc.counters_bytes, s) != cudaSuccess)
         return SPMM_ERR_CUDA;
     LaunchOpts o;

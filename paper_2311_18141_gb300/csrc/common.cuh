@@ -282,6 +282,9 @@ struct Problem {
     int32_t* piece_cnt;       // [chunks*TC]
     float* slots;             // [2*chunks][N]
     int32_t* status;          // status words
+    // optional per-warp trace (null: off)
+    spmm_trace_record* trace;
+    int32_t trace_max;
 };
 
 // Workspace layout (offsets in bytes from the workspace base).

@@ -604,7 +604,15 @@ __device__ __forceinline__ uint32_t warp_staging(int lane, uint32_t& bar0,
     return smem + (uint32_t)(warps * 16 + w * stage_bytes);
 }
 
-// The persistent kernel: each warp is an independent worker.
+__device__ __forceinline__ long long globaltimer_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// The persistent kernel: each warp is an independent worker.  With a trace
+// buffer (p.trace), lane 0 of every warp records its start and end time, the
+// units it walked and how many of them came from outside its home tile (row).
 template <class TA, class TB, int LPN, int VPL>
 __global__ void __launch_bounds__(256, (KCfg<TA, TB, LPN, VPL>::MINB))
 spmm_csr_persistent(const Problem p, int flags) {
@@ -614,6 +622,8 @@ spmm_csr_persistent(const Problem p, int flags) {
     const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     uint32_t bar0 = 0, phases = 0;
     const uint32_t wbase = warp_staging<K>(lane, bar0);
+    if (p.trace && lane == 0 && warp < p.trace_max) p.trace[warp].t_start_ns = globaltimer_ns();
+    int units = 0, stolen = 0;
     if (flags & kFlagInterleave) {
         // ticket k of tile row i is chunk k / TC of tile (i, k % TC); the
         // tile row's first counter is its queue
@@ -634,43 +644,64 @@ spmm_csr_persistent(const Problem p, int flags) {
                 const int j = k - c * p.TC;
                 const LaneCols<K::VPL> lc = lane_cols<K, K::VPL, K::LPN>(p, j, lane % K::LPN);
                 const int cs = c * K::G + g;
+                ++units;
+                stolen += step != 0;
                 if (!walk_unit<K>(p, i, j, cs < nsub ? cs : -1, lc, lane, wbase, bar0, phases))
-                    return;
+                    goto done;
             }
         }
-        return;
+    } else {
+        const int T = p.TR * p.TC;
+        const bool sweep = (flags & kFlagSweep) != 0;
+        const int home = (flags & kFlagLockstep) ? 0
+                         : sweep ? (int)blockIdx.x % p.TR
+                                 : ((flags & kFlagWarpHome) ? warp : (int)blockIdx.x) % T;
+        for (int step = 0; step < T; ++step) {
+            int t = home + step;
+            if (t >= T) t -= T;
+            int i, j;
+            if (sweep || (flags & kFlagOrderColumn)) {
+                j = t / p.TR;
+                i = t - j * p.TR;
+            } else {
+                i = t / p.TC;
+                j = t - i * p.TC;
+            }
+            const int tid = i * p.TC + j;
+            const int nsub = p.blk_base[i + 1] - p.blk_base[i];
+            const int nun = (nsub + K::G - 1) / K::G;   // units: G sub-chunks each
+            if (nun == 0) continue;
+            if (ld_relaxed(p.tile_ctr + tid) >= nun) continue;
+            const LaneCols<K::VPL> lc = lane_cols<K, K::VPL, K::LPN>(p, j, lane % K::LPN);
+            while (true) {
+                int c = 0;
+                if (lane == 0) c = atomicAdd(p.tile_ctr + tid, 1);
+                c = __shfl_sync(kFull, c, 0);
+                if (c >= nun) break;
+                const int cs = c * K::G + g;
+                ++units;
+                stolen += step != 0;
+                if (!walk_unit<K>(p, i, j, cs < nsub ? cs : -1, lc, lane, wbase, bar0, phases))
+                    goto done;
+            }
+        }
     }
-    const int T = p.TR * p.TC;
-    const bool sweep = (flags & kFlagSweep) != 0;
-    const int home = (flags & kFlagLockstep) ? 0
-                     : sweep ? (int)blockIdx.x % p.TR
-                             : ((flags & kFlagWarpHome) ? warp : (int)blockIdx.x) % T;
-    for (int step = 0; step < T; ++step) {
-        int t = home + step;
-        if (t >= T) t -= T;
-        int i, j;
-        if (sweep || (flags & kFlagOrderColumn)) {
-            j = t / p.TR;
-            i = t - j * p.TR;
-        } else {
-            i = t / p.TC;
-            j = t - i * p.TC;
-        }
-        const int tid = i * p.TC + j;
-        const int nsub = p.blk_base[i + 1] - p.blk_base[i];
-        const int nun = (nsub + K::G - 1) / K::G;   // units: G sub-chunks each
-        if (nun == 0) continue;
-        if (ld_relaxed(p.tile_ctr + tid) >= nun) continue;
-        const LaneCols<K::VPL> lc = lane_cols<K, K::VPL, K::LPN>(p, j, lane % K::LPN);
-        while (true) {
-            int c = 0;
-            if (lane == 0) c = atomicAdd(p.tile_ctr + tid, 1);
-            c = __shfl_sync(kFull, c, 0);
-            if (c >= nun) break;
-            const int cs = c * K::G + g;
-            if (!walk_unit<K>(p, i, j, cs < nsub ? cs : -1, lc, lane, wbase, bar0, phases))
-                return;
-        }
+done:
+    if (p.trace && lane == 0 && warp < p.trace_max) {
+        // the home tile (row) of the walk above, recomputed
+        int home;
+        if (flags & kFlagLockstep) home = 0;
+        else if (flags & kFlagInterleave) home = (int)blockIdx.x % p.TR;
+        else if (flags & kFlagSweep) home = (int)blockIdx.x % p.TR;
+        else home = ((flags & kFlagWarpHome) ? warp : (int)blockIdx.x) % (p.TR * p.TC);
+        uint32_t smid;
+        asm("mov.u32 %0, %%smid;" : "=r"(smid));
+        spmm_trace_record* r = p.trace + warp;
+        r->t_end_ns = globaltimer_ns();
+        r->units = units;
+        r->stolen = stolen;
+        r->home = home;
+        r->smid = (int32_t)smid;
     }
 }
 

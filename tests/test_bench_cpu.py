@@ -7,6 +7,7 @@ import socket
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 import torch
 import torch.distributed as dist
@@ -109,3 +110,20 @@ def test_tile_imbalance_is_max_over_mean_of_row_blocks():
     # ragged: 3 blocks of ceil(8/3) = 3 rows: 6, 4, 2 -> 6 / 4
     assert abs(bench.tile_nnz_imbalance(rowptr, 8, 3) - 1.5) < 1e-12
     assert bench.tile_nnz_imbalance(torch.zeros(9, dtype=torch.int32), 8, 4) == 1.0
+
+
+def test_trace_summary_of_hand_made_records():
+    from paper_2311_18141_gb300 import binding
+    rec = np.zeros(3, dtype=binding.TRACE_DTYPE)
+    rec["t_start_ns"] = [10, 10, 20]
+    rec["t_end_ns"] = [110, 60, 120]
+    rec["units"] = [4, 2, 6]
+    rec["stolen"] = [1, 0, 2]
+    t = bench.trace_summary(rec)
+    assert t["warps"] == 3 and t["launch_us"] == 0.11
+    assert abs(t["busy_max_over_avg"] - 100 / (250 / 3)) < 1e-12      # busy 100, 50, 100
+    assert abs(t["finish_spread_us"] - 0.06) < 1e-12
+    assert abs(t["idle_share"] - (1 - 250 / 330)) < 1e-12
+    assert abs(t["units_per_warp_max_over_avg"] - 1.5) < 1e-12
+    assert abs(t["stolen_share"] - 0.25) < 1e-12
+    assert bench.trace_summary(rec[:0]) is None

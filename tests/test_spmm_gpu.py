@@ -246,3 +246,43 @@ def test_every_unit_reserved_exactly_once_under_imbalance(tile_order):
     C, st = run_spmm(A, B, N, tile_rows=16, tile_cols=4, chunk_items=32, tile_order=tile_order)
     assert st == 0
     assert torch.equal(C[:, 0], torch.from_numpy(lens.astype(np.float32)))
+
+
+@pytest.mark.parametrize("tile_order", [0, 16])
+def test_trace_records_account_for_every_unit(tile_order):
+    """A traced launch computes the same C bit for bit; its per-warp records
+    cover every work unit once (units of G = 32/LPN chunks per tile, summed over
+    tiles), stolen units are a subset, times are ordered and SM ids valid."""
+    A = inputs.rmat_csr(14, 16, seed=77)
+    N, TR, TC = 128, 16, 4
+    Ad = A.to("cuda")
+    B = inputs.dense_normal(A.K, N, seed=78, device="cuda")
+    plan = binding.Plan(Ad.rowptr, A.M, A.K, A.nnz, N, TR, TC,
+                        tuning=binding.make_tuning(tile_order=tile_order))
+    ws = binding.workspace(plan.workspace_bytes)
+    C0 = torch.empty(A.M, N, device="cuda")
+    binding.spmm_csr(Ad.rowptr, Ad.colind, Ad.vals, B, C0, A.M, A.K, N, A.nnz, plan=plan, ws=ws)
+    buf = binding.trace_buffer(1 << 15)
+    plan.set_trace(buf)
+    C1 = torch.empty_like(C0)
+    binding.spmm_csr(Ad.rowptr, Ad.colind, Ad.vals, B, C1, A.M, A.K, N, A.nnz, plan=plan, ws=ws)
+    torch.cuda.synchronize()
+    assert binding.spmm_get_device_status(ws) == 0
+    assert torch.equal(C0, C1)
+    rec = binding.read_trace(buf)
+    assert rec.size > 0
+    # units: per row block, ceil(chunks / G) units in each of the TC column blocks (G = 4 here)
+    chunks, _ = plan.units()
+    total = int(rec["units"].sum())
+    assert chunks * TC / 4 <= total <= chunks * TC / 4 + TR * TC
+    assert np.all(rec["stolen"] <= rec["units"]) and np.all(rec["stolen"] >= 0)
+    assert np.all(rec["t_end_ns"] >= rec["t_start_ns"]) and np.all(rec["t_start_ns"] > 0)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert np.all((rec["smid"] >= 0) & (rec["smid"] < sms))
+    # tracing off: the buffer is left alone
+    plan.set_trace(None)
+    buf.zero_()
+    binding.spmm_csr(Ad.rowptr, Ad.colind, Ad.vals, B, C1, A.M, A.K, N, A.nnz, plan=plan, ws=ws)
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(buf) == 0
+    plan.close()
