@@ -419,11 +419,27 @@ class Batch:
         _check(load_library().spmm_batch_graph_launch(self.handle, _ptr(ws), ws.numel(),
                                                       _stream(stream)), "spmm_batch_graph_launch")
 
-    def autotune(self, ws, reps=3, stream=None) -> float:
+    def autotune(self, ws, reps=3, stream=None, cache: str | None = None) -> float:
+        """Tune the per-size-class shapes (spmm_batch_autotune) and return the
+        best time in ms.  With ``cache`` (a JSON path), shapes stored there for
+        a batch of the same signature are set instead of tuning, and newly
+        tuned shapes are stored."""
+        from . import tuning_cache
+        sig = None
+        self.last_tune_from_cache = False
+        if cache is not None:
+            sig = tuning_cache.batch_signature(self._keep, torch.cuda.get_device_name())
+            hit = tuning_cache.load(cache, sig, self.count)
+            if hit is not None:
+                self.set_shapes(hit["tile_rows"], hit["tile_cols"], hit["chunk_items"], stream)
+                self.last_tune_from_cache = True
+                return hit["ms"]
         ms = ctypes.c_float()
         _check(load_library().spmm_batch_autotune(self.handle, _ptr(ws), ws.numel(), int(reps),
                                                   _stream(stream), ctypes.byref(ms)),
                "spmm_batch_autotune")
+        if cache is not None:
+            tuning_cache.store(cache, sig, *self.shapes(), float(ms.value))
         return float(ms.value)
 
     def shapes(self):

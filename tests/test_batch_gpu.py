@@ -104,3 +104,27 @@ def test_batch_rejects_mixed_or_bad_problems():
     with pytest.raises(binding.SpmmError) as e:
         binding.Batch(probs)
     assert e.value.status == binding.SPMM_ERR_MISALIGNED
+
+
+def test_autotune_cache_round_trip(tmp_path):
+    """Tuned shapes are stored under the batch's signature; a new batch over the
+    same problems sets them from the cache (no tuning) and still computes the
+    oracle's products."""
+    path = str(tmp_path / "tune.json")
+    probs, host = make_batch(16, seed=73, dtype=torch.bfloat16, widths=(16, 64, 128))
+    batch = binding.Batch(probs)
+    ws = binding.workspace(batch.workspace_bytes)
+    ms = batch.autotune(ws, cache=path)
+    assert ms > 0 and not batch.last_tune_from_cache
+    tuned = batch.shapes()
+    batch.close()
+    again = binding.Batch(probs)
+    assert again.autotune(ws, cache=path) == pytest.approx(ms)
+    assert again.last_tune_from_cache and again.shapes() == tuned
+    for q in probs:
+        q["C"].fill_(float("nan"))
+    again.graph_launch(ws)
+    torch.cuda.synchronize()
+    assert binding.spmm_get_device_status(ws) == 0
+    check(probs, host, "batch with cached shapes")
+    again.close()
