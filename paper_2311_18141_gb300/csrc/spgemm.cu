@@ -10,8 +10,10 @@
 //      once, stably, carrying the value; otherwise the products are sorted
 //      stably by column, then stably by row, carrying each product's index.
 //      Either way equal (i, j) stay in expansion order.
-//   4. compress: runs of equal (i, j) are summed in FP32 in that order, one
-//      entry of C each; row pointers by lower bound over the entry rows.
+//   4. compress: run heads are flagged and scanned into entry indices, each
+//      entry's first product is recorded, and one thread per entry sums its
+//      run in FP32 in that order; row pointers by lower bound over the entry
+//      rows.
 // An entry of C exists wherever some product is formed (explicit zeros
 // count).  The order of every sum is fixed, so results are reproducible.
 #include <string.h>
@@ -129,22 +131,31 @@ __global__ void spgemm_heads_fused_kernel(const uint32_t* __restrict__ key, int6
         head[p] = p < P && (p == 0 || key[p] != key[p - 1]);
 }
 
+// start[q] = first product of entry q (pos[p] for the run heads p), start[E] = P,
+// where E = pos[P] is the entry count.
+__global__ void spgemm_run_starts_kernel(const int32_t* __restrict__ pos, int64_t P,
+                                         int32_t* __restrict__ start) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += stride)
+        if (pos[p + 1] != pos[p]) start[pos[p]] = (int32_t)p;
+    if (blockIdx.x == 0 && threadIdx.x == 0) start[pos[P]] = (int32_t)P;
+}
+
+// One thread per entry q: the FP32 sum of its products start[q] .. start[q+1]-1
+// in order (the loop bounds are known before any value is loaded).
 __global__ void spgemm_compress_fused_kernel(const uint32_t* __restrict__ key,
                                              const float* __restrict__ val,
-                                             const int32_t* __restrict__ pos, int64_t P, int bN,
+                                             const int32_t* __restrict__ start,
+                                             const int32_t* __restrict__ nentries, int bN,
                                              int32_t* __restrict__ crow, int32_t* __restrict__ ccol,
                                              float* __restrict__ cval) {
+    const int64_t E = *nentries;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += stride) {
-        if (pos[p + 1] == pos[p]) continue;   // not the first product of its run
-        const int32_t q = pos[p];
-        float sum = val[p];
-        int64_t x = p + 1;
-        while (x < P && pos[x + 1] == pos[x]) {
-            sum += val[x];
-            ++x;
-        }
-        const uint32_t kk = key[p];
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < E; q += stride) {
+        const int32_t s0 = start[q], s1 = start[q + 1];
+        float sum = val[s0];
+        for (int32_t x = s0 + 1; x < s1; ++x) sum += val[x];
+        const uint32_t kk = key[s0];
         crow[q] = (int32_t)(kk >> bN);
         ccol[q] = (int32_t)(kk & ((1u << bN) - 1u));
         cval[q] = sum;
@@ -179,33 +190,30 @@ __global__ void spgemm_heads_kernel(const int32_t* __restrict__ rows,
     }
 }
 
-// One thread per run: sum the run's products in order; entry pos[p].
+// One thread per entry q: sum its products start[q] .. start[q+1]-1 in order.
 __global__ void spgemm_compress_kernel(const int32_t* __restrict__ rows,
                                        const int32_t* __restrict__ idx,
                                        const int32_t* __restrict__ pcol,
                                        const float* __restrict__ pval,
-                                       const int32_t* __restrict__ pos, int64_t P,
+                                       const int32_t* __restrict__ start,
+                                       const int32_t* __restrict__ nentries,
                                        int32_t* __restrict__ crow, int32_t* __restrict__ ccol,
                                        float* __restrict__ cval) {
+    const int64_t E = *nentries;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < P; p += stride) {
-        if (pos[p + 1] == pos[p]) continue;   // not the first product of its run
-        const int32_t q = pos[p];
-        float sum = pval[idx[p]];
-        int64_t x = p + 1;
-        while (x < P && pos[x + 1] == pos[x]) {
-            sum += pval[idx[x]];
-            ++x;
-        }
-        crow[q] = rows[p];
-        ccol[q] = pcol[idx[p]];
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < E; q += stride) {
+        const int32_t s0 = start[q], s1 = start[q + 1];
+        float sum = pval[idx[s0]];
+        for (int32_t x = s0 + 1; x < s1; ++x) sum += pval[idx[x]];
+        crow[q] = rows[s0];
+        ccol[q] = pcol[idx[s0]];
         cval[q] = sum;
     }
 }
 
 // Workspace: [status word, 256 B][arrays ...]
 struct SpgemmLayout {
-    size_t row_of, off, scan, prow, pcol, pval, k0, v0, k1, v1, rkey, icopy, pos, radix,
+    size_t row_of, off, scan, prow, pcol, pval, k0, v0, k1, v1, rkey, icopy, pos, start, radix,
         crow, ccol, cval, total;
 };
 
@@ -229,6 +237,7 @@ SpgemmLayout spgemm_layout(int64_t nnzA, int64_t P, int64_t M, int64_t N) {
     L.rkey = o; o += b;
     L.icopy = o; o += b;
     L.pos = o; o += up256(4 * (size_t)(P + 1));
+    L.start = o; o += up256(4 * (size_t)(P + 1));
     L.crow = o; o += b;
     L.ccol = o; o += b;
     L.cval = o; o += b;
@@ -343,8 +352,9 @@ extern "C" int spmm_spgemm(const int32_t* A_rowptr, const int32_t* A_colind, con
             spgemm_heads_fused_kernel<<<grid_for(P + 1, 256), 256, 0, s>>>(skey, P, I(L.pos));
             if (scan_exclusive_i32(I(L.pos), P + 1, ws + L.radix, s) != cudaSuccess)
                 return SPMM_ERR_CUDA;
+            spgemm_run_starts_kernel<<<grid_for(P, 256), 256, 0, s>>>(I(L.pos), P, I(L.start));
             spgemm_compress_fused_kernel<<<grid_for(P, 256), 256, 0, s>>>(
-                skey, sval, I(L.pos), P, bN, I(L.crow), I(L.ccol),
+                skey, sval, I(L.start), I(L.pos) + P, bN, I(L.crow), I(L.ccol),
                 reinterpret_cast<float*>(ws + L.cval));
         } else {
         spgemm_expand_kernel<<<grid_for(nnzA * 32, 256), 256, 0, s>>>(
@@ -367,9 +377,10 @@ extern "C" int spmm_spgemm(const int32_t* A_rowptr, const int32_t* A_colind, con
                                                                  I(L.pos));
         if (scan_exclusive_i32(I(L.pos), P + 1, ws + L.radix, s) != cudaSuccess)
             return SPMM_ERR_CUDA;
+        spgemm_run_starts_kernel<<<grid_for(P, 256), 256, 0, s>>>(I(L.pos), P, I(L.start));
         spgemm_compress_kernel<<<grid_for(P, 256), 256, 0, s>>>(
-            rows, idx, I(L.pcol), reinterpret_cast<const float*>(ws + L.pval), I(L.pos), P,
-            I(L.crow), I(L.ccol), reinterpret_cast<float*>(ws + L.cval));
+            rows, idx, I(L.pcol), reinterpret_cast<const float*>(ws + L.pval), I(L.start),
+            I(L.pos) + P, I(L.crow), I(L.ccol), reinterpret_cast<float*>(ws + L.cval));
         }
         if (cudaGetLastError() != cudaSuccess) return SPMM_ERR_CUDA;
     }
