@@ -363,7 +363,8 @@ typedef struct spmm_host_pipe_s* spmm_host_pipe;
  *   N and tile grid): depth (1..4) slots of (M+1) + nnz int32, nnz elements
  *   of a_dtype, K x N elements of b_dtype (dense, ldb = N) and M x N float
  *   (ldc = N), plus the plan's workspace.  N must meet the vector-path rule of
- *   b_dtype.  The plan must outlive the pipeline.  Allocates device memory and
+ *   b_dtype.  No row scales are carried: b_dtype E4M3 returns
+ *   SPMM_ERR_UNSUPPORTED.  The plan must outlive the pipeline.  Allocates device memory and
  *   creates two streams and 3 * depth events; *pipe is NULL on failure.
  */
 int spmm_host_pipe_create(spmm_host_pipe* pipe, spmm_plan plan, int32_t a_dtype,

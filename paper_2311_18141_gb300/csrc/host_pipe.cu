@@ -72,7 +72,9 @@ int spmm_host_pipe_create(spmm_host_pipe* pipe, spmm_plan plan, int32_t a_dtype,
     *pipe = nullptr;
     if (!plan || depth < 1 || depth > kMaxDepth) return SPMM_ERR_INVALID_ARG;
     const int ea = elem_bytes(a_dtype), eb = elem_bytes(b_dtype);
-    if (ea == 0 || eb == 0) return SPMM_ERR_UNSUPPORTED;
+    // E4M3 B only means something with its per-row scales, which the pipeline
+    // does not carry
+    if (ea == 0 || eb == 0 || b_dtype == SPMM_E4M3) return SPMM_ERR_UNSUPPORTED;
     spmm_host_pipe_s* p = new (std::nothrow) spmm_host_pipe_s();
     if (!p) return SPMM_ERR_INVALID_ARG;
     plan_shape(plan, &p->M, &p->K, &p->nnz, &p->N, nullptr, nullptr);

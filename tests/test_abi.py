@@ -111,6 +111,8 @@ def test_host_argument_checks_return_before_device_work(lib):
                                      None) == binding.SPMM_ERR_INVALID_ARG
     assert lib.spmm_host_pipe_create(ctypes.byref(h), fake, 7, 0, 2,
                                      None) == binding.SPMM_ERR_UNSUPPORTED
+    assert lib.spmm_host_pipe_create(ctypes.byref(h), fake, 0, binding.SPMM_E4M3, 2,
+                                     None) == binding.SPMM_ERR_UNSUPPORTED
     assert lib.spmm_host_pipe_submit(None, fake, fake, fake, fake,
                                      fake) == binding.SPMM_ERR_INVALID_ARG
     assert lib.spmm_host_pipe_wait(None) == binding.SPMM_ERR_INVALID_ARG
