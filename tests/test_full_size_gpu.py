@@ -163,3 +163,50 @@ def test_batch_512_graph_autotuned_sampled():
         bound = oracle.abs_bound(sub_rp, sub_ci, v, b)
         assert_close_rel(got, ref, bound, TOL_F32, f"batch product {k}")
     batch.close()
+
+
+def test_max_size_nnz_near_int32_limit():
+    """The largest nonzero count the API takes (2^31 - 8 here, with 2^28 - 1 rows
+    of 8), so merge-path positions (rows + nonzeros, about 2.4e9) pass 2^31:
+    the plan's 64-bit coordinates and the kernel's 32-bit per-chunk offsets are
+    both exercised.  Columns are hashed (repeats allowed, unsorted), B is 2^20 x 4.
+    Sampled rows, including both ends of every row block, against the oracle."""
+    dev = torch.device("cuda")
+    free, _ = torch.cuda.mem_get_info()
+    if free < 80 * (1 << 30):
+        pytest.skip("needs about 80 GB of free device memory")
+    per, M, K, N, TR = 8, (1 << 28) - 1, 1 << 20, 4, 16
+    nnz = M * per
+    assert nnz == (1 << 31) - 8
+    rowptr = (torch.arange(M + 1, dtype=torch.int64, device=dev) * per).to(torch.int32)
+    colind = torch.empty(nnz, dtype=torch.int32, device=dev)
+    vals = torch.empty(nnz, dtype=torch.float32, device=dev)
+    step = 1 << 27
+    for lo in range(0, nnz, step):
+        e = torch.arange(lo, min(nnz, lo + step), dtype=torch.int64, device=dev)
+        colind[lo:lo + e.numel()] = ((e * 2654435761) % K).to(torch.int32)
+        vals[lo:lo + e.numel()] = (e % 1021).to(torch.float32) / 1021.0 - 0.5
+        del e
+    B = inputs.dense_normal(K, N, seed=91, device=dev)
+    C = torch.full((M, N), float("nan"), device=dev)
+    plan = binding.Plan(rowptr, M, K, nnz, N, TR, 1)
+    ws = binding.workspace(plan.workspace_bytes, dev)
+    binding.spmm_csr(rowptr, colind, vals, B, C, M, K, N, nnz, plan=plan, ws=ws)
+    torch.cuda.synchronize()
+    assert binding.spmm_get_device_status(ws) == 0
+    rb = -(-M // TR)
+    edges = [x for i in range(TR + 1) for x in (i * rb - 1, i * rb) if 0 <= x < M]
+    rng = np.random.default_rng(92)
+    rows = np.unique(np.concatenate([rng.choice(M, 2000, replace=False), edges, [0, M - 1]]))
+    rows_d = torch.from_numpy(rows).to(dev)
+    idx = (rows_d.to(torch.int64) * per)[:, None] + torch.arange(per, device=dev)[None, :]
+    cols = colind[idx.flatten()].cpu().numpy()
+    v = vals[idx.flatten()].cpu().numpy()
+    ucols, local = np.unique(cols, return_inverse=True)
+    sub_rp = np.arange(rows.size + 1, dtype=np.int32) * per
+    b = B[torch.from_numpy(ucols).to(dev)].cpu().numpy()
+    ref = oracle.spmm(sub_rp, local.astype(np.int32), v, b)
+    bound = oracle.abs_bound(sub_rp, local.astype(np.int32), v, b)
+    got = C[rows_d].cpu().numpy()
+    assert_close_rel(got, ref, bound, TOL_F32, "nnz = 2^31 - 8")
+    plan.close()
