@@ -129,6 +129,17 @@ int spmm_plan_workspace_size(spmm_plan plan, size_t* bytes);
 int spmm_plan_units(spmm_plan plan, int64_t* chunks, int64_t* units);
 
 /*
+ * spmm_plan_get_boundaries -- copy a plan's partition to host buffers
+ *   (synchronous).  blk_base[TR+1]: chunks before row block i; for row block
+ *   i, boundary c (0 <= c <= chunks of the block) sits at index
+ *   blk_base[i] + i + c of bnd_row / bnd_nnz (int32[chunks + TR]), the merge-
+ *   path point (rows finished, nonzeros consumed) where chunk c starts.  Any
+ *   output may be NULL.  Meant for inspection and tests.
+ */
+int spmm_plan_get_boundaries(spmm_plan plan, int32_t* blk_base, int32_t* bnd_row,
+                             int32_t* bnd_nnz);
+
+/*
  * Per-warp trace of the persistent SpMM kernel: the on-chip counterpart of the
  * paper's split of run time into computation and load imbalance (Section 6).
  * Each warp of a spmm_csr launch with a traced plan writes one record, warp w

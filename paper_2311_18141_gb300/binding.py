@@ -41,6 +41,7 @@ EXPORTED = [
     "spmm_batch_graph_launch", "spmm_batch_autotune", "spmm_spgemm_analyze", "spmm_spgemm",
     "spmm_spgemm_copy", "spmm_host_pipe_create", "spmm_host_pipe_submit", "spmm_host_pipe_wait",
     "spmm_host_pipe_destroy", "spmm_selftest_wait_timeout", "spmm_plan_set_trace",
+    "spmm_plan_get_boundaries",
 ]
 
 # spmm_trace_record: per-warp record of a traced spmm_csr launch
@@ -123,6 +124,7 @@ def load_library(path: str | None = None):
         lib.spmm_batch_autotune.argtypes = [vp, vp, sz, i32, vp, P(ctypes.c_float)]
         lib.spmm_selftest_wait_timeout.argtypes = [vp, sz, i64, vp]
         lib.spmm_plan_set_trace.argtypes = [vp, vp, i32]
+        lib.spmm_plan_get_boundaries.argtypes = [vp, vp, vp, vp]
         lib.spmm_host_pipe_create.argtypes = [P(vp), vp, i32, i32, i32, vp]
         lib.spmm_host_pipe_submit.argtypes = [vp, vp, vp, vp, vp, vp]
         lib.spmm_host_pipe_wait.argtypes = [vp]
@@ -218,6 +220,17 @@ class Plan:
         _check(load_library().spmm_plan_set_trace(self.handle, _ptr(records), int(n)),
                "spmm_plan_set_trace")
         self._trace = records   # the plan writes into it: keep it alive
+
+    def boundaries(self):
+        """(blk_base[TR+1], bnd_row, bnd_nnz) of the plan as numpy int32 arrays."""
+        chunks, _ = self.units()
+        bb = np.empty(self.tile_rows + 1, np.int32)
+        br = np.empty(chunks + self.tile_rows, np.int32)
+        bz = np.empty(chunks + self.tile_rows, np.int32)
+        _check(load_library().spmm_plan_get_boundaries(
+            self.handle, bb.ctypes.data_as(ctypes.c_void_p), br.ctypes.data_as(ctypes.c_void_p),
+            bz.ctypes.data_as(ctypes.c_void_p)), "spmm_plan_get_boundaries")
+        return bb, br, bz
 
     def units(self) -> tuple[int, int]:
         c, u = ctypes.c_int64(), ctypes.c_int64()

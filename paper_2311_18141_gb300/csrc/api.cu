@@ -188,6 +188,23 @@ int spmm_plan_destroy(spmm_plan plan) {
     return SPMM_OK;
 }
 
+int spmm_plan_get_boundaries(spmm_plan plan, int32_t* blk_base, int32_t* bnd_row,
+                             int32_t* bnd_nnz) {
+    if (!plan) return SPMM_ERR_INVALID_ARG;
+    int32_t n = 0;
+    if (cudaMemcpy(&n, plan->blk_base + plan->TR, sizeof(n), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return SPMM_ERR_CUDA;
+    const size_t nb = (size_t)n + plan->TR;
+    if ((blk_base && cudaMemcpy(blk_base, plan->blk_base, 4 * ((size_t)plan->TR + 1),
+                                cudaMemcpyDeviceToHost) != cudaSuccess) ||
+        (bnd_row && cudaMemcpy(bnd_row, plan->bnd_row, 4 * nb, cudaMemcpyDeviceToHost) !=
+                        cudaSuccess) ||
+        (bnd_nnz && cudaMemcpy(bnd_nnz, plan->bnd_nnz, 4 * nb, cudaMemcpyDeviceToHost) !=
+                        cudaSuccess))
+        return SPMM_ERR_CUDA;
+    return SPMM_OK;
+}
+
 int spmm_plan_set_trace(spmm_plan plan, spmm_trace_record* records, int32_t max_records) {
     if (!plan || max_records < 0) return SPMM_ERR_INVALID_ARG;
     plan->trace = max_records > 0 ? records : nullptr;

@@ -117,6 +117,7 @@ def test_host_argument_checks_return_before_device_work(lib):
                                      fake) == binding.SPMM_ERR_INVALID_ARG
     assert lib.spmm_host_pipe_wait(None) == binding.SPMM_ERR_INVALID_ARG
     assert lib.spmm_host_pipe_destroy(None) == binding.SPMM_OK
+    assert lib.spmm_plan_get_boundaries(None, None, None, None) == binding.SPMM_ERR_INVALID_ARG
     # bounded-wait self-test: workspace and limit are checked on the host
     assert lib.spmm_selftest_wait_timeout(None, 0, 1024, None) == binding.SPMM_ERR_WORKSPACE
     assert lib.spmm_selftest_wait_timeout(fake, 8, 1024, None) == binding.SPMM_ERR_WORKSPACE
