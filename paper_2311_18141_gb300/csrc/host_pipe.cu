@@ -34,6 +34,22 @@ struct Slot {
 
 size_t round256(size_t b) { return (b + 255) / 256 * 256; }
 
+// Copies go out in pieces of at most kCopyPiece bytes, so that uploads and
+// downloads on the two copy streams interleave finely instead of one copy
+// engine holding a multi-gigabyte transfer.
+constexpr size_t kCopyPiece = (size_t)64 << 20;
+
+cudaError_t copy_pieces(void* dst, const void* src, size_t bytes, cudaMemcpyKind kind,
+                        cudaStream_t s) {
+    for (size_t off = 0; off < bytes; off += kCopyPiece) {
+        const size_t n = bytes - off < kCopyPiece ? bytes - off : kCopyPiece;
+        const cudaError_t e = cudaMemcpyAsync(static_cast<char*>(dst) + off,
+                                              static_cast<const char*>(src) + off, n, kind, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 }  // namespace
 
 struct spmm_host_pipe_s {
@@ -139,12 +155,12 @@ int spmm_host_pipe_submit(spmm_host_pipe p, const int32_t* A_rowptr, const int32
     const auto ok = [](cudaError_t e) { return e == cudaSuccess; };
     // copy-in: the slot's inputs are free once step k - depth's product is done
     if (s.used && !ok(cudaStreamWaitEvent(p->in, s.comp_done, 0))) return SPMM_ERR_CUDA;
-    if (!ok(cudaMemcpyAsync(s.rowptr, A_rowptr, p->rp_bytes, cudaMemcpyHostToDevice, p->in)))
+    if (!ok(copy_pieces(s.rowptr, A_rowptr, p->rp_bytes, cudaMemcpyHostToDevice, p->in)))
         return SPMM_ERR_CUDA;
     if (p->nnz > 0 &&
-        (!ok(cudaMemcpyAsync(s.colind, A_colind, p->ci_bytes, cudaMemcpyHostToDevice, p->in)) ||
-         !ok(cudaMemcpyAsync(s.vals, A_vals, p->v_bytes, cudaMemcpyHostToDevice, p->in)) ||
-         !ok(cudaMemcpyAsync(s.B, B, p->b_bytes, cudaMemcpyHostToDevice, p->in))))
+        (!ok(copy_pieces(s.colind, A_colind, p->ci_bytes, cudaMemcpyHostToDevice, p->in)) ||
+         !ok(copy_pieces(s.vals, A_vals, p->v_bytes, cudaMemcpyHostToDevice, p->in)) ||
+         !ok(copy_pieces(s.B, B, p->b_bytes, cudaMemcpyHostToDevice, p->in))))
         return SPMM_ERR_CUDA;
     if (!ok(cudaEventRecord(s.in_done, p->in))) return SPMM_ERR_CUDA;
     // product: needs this step's inputs, and step k - depth's C out of the slot
@@ -157,7 +173,7 @@ int spmm_host_pipe_submit(spmm_host_pipe p, const int32_t* A_rowptr, const int32
     if (!ok(cudaEventRecord(s.comp_done, p->comp))) return SPMM_ERR_CUDA;
     // copy-out
     if (!ok(cudaStreamWaitEvent(p->out, s.comp_done, 0)) ||
-        !ok(cudaMemcpyAsync(C, s.C, p->c_bytes, cudaMemcpyDeviceToHost, p->out)) ||
+        !ok(copy_pieces(C, s.C, p->c_bytes, cudaMemcpyDeviceToHost, p->out)) ||
         !ok(cudaEventRecord(s.out_done, p->out)))
         return SPMM_ERR_CUDA;
     s.used = true;
