@@ -61,6 +61,23 @@ def test_brute_force_exact(shape, density):
     np.testing.assert_allclose(C, dense @ B, rtol=1e-12, atol=1e-12)
 
 
+@pytest.mark.parametrize("threads", [1, 3])
+def test_abs_bound_is_the_product_of_absolute_values(threads):
+    """The tolerance scale |A|.|B|: brute force over |A| and |B|, the same for
+    one thread or several, and never below |A.B|."""
+    rng = np.random.default_rng(5150)
+    rp, ci, v, dense = random_csr(rng, 19, 11, 0.4)
+    B = rng.standard_normal((11, 6))
+    prev = oracle.get_threads()
+    oracle.set_threads(threads)
+    try:
+        bound = oracle.abs_bound(rp, ci, v, B)
+    finally:
+        oracle.set_threads(prev)
+    np.testing.assert_array_equal(bound, brute_force(np.abs(dense), np.abs(B)))
+    assert np.all(bound >= np.abs(oracle.spmm(rp, ci, v, B)))
+
+
 def test_golden_hand_worked():
     fields = {}
     with open(os.path.join(GOLDEN, "spmm_3x4.txt")) as f:
