@@ -36,8 +36,8 @@ WORKLOAD = "rmat-s22-ef16-n128-fp32-grid16x4"
 NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e nominal bandwidth, for the second roofline fraction
 FALLBACK_HBM_GBS = 6800.0
 PROFILE = os.path.join(ROOT, "profiles", "spmm_csr_persistent_rmat_s22_n128.md")
-KERNEL_SOURCES = ["common.cuh", "spmm_kernel.cuh", "spmm_launch_impl.cuh", "spmm_f32_f32.cu",
-                  "plan.cu"]
+KERNEL_SOURCES = ["common.cuh", "schedule.cuh", "spmm_wide.cuh", "spmm_launch_impl.cuh",
+                  "spmmw_f32_f32.cu", "plan.cu"]
 
 
 def parse():
@@ -54,16 +54,21 @@ def parse():
     ap.add_argument("--order", type=int, default=16,
                     help="spmm_tuning.tile_order (16: one queue per tile row, chunks of its "
                          "tiles handed out in turn)")
+    ap.add_argument("--kernel", type=int, default=0,
+                    help="spmm_tuning.kernel: 0 library default, 1 staged 16-byte kernel, "
+                         "2 32-byte-lane kernel")
     ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the precision (FP32/BF16/E4M3 B) and small-workload objects")
     ap.add_argument("--context", action="store_true",
                     help="also time torch.sparse.mm (cuSPARSE) on the same product, as context")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--spgemm-scale", type=int, default=14,
                     help="R-MAT scale of the A*A SpGEMM workload")
     ap.add_argument("--workload", default="rmat",
-                    choices=["rmat", "precision", "gcn", "batch", "spgemm", "loadsim"],
+                    choices=["rmat", "precision", "gcn", "batch", "spgemm", "loadsim", "gather"],
                     help="rmat: the benchmark line; the others report the precision, "
                          "backward and batched forms")
     return ap.parse_args()
@@ -91,17 +96,27 @@ def stored_traffic(src_hash: str):
     return float(m_traffic.group(1))
 
 
-def kernel_shape(N, TC, epv=4):
-    """(lanes per nonzero, vectors per lane) the library picks for FP32 B."""
+def kernel_name(N, TC, esz=4, kernel=0, tag="TagF32"):
+    """The persistent kernel the library launches for FP32 A and B of element
+    size `esz` (aligned torch tensors, dense strides): the staged kernel by
+    default, the 32-byte-lane kernel when asked for (kernel 2) and a column
+    block is 2..32 whole 32-byte vectors."""
+    epv = 16 // esz
     w = -(-N // TC)
     w = -(-w // epv) * epv
-    nvec = w // epv
+    nb = w * esz
+    if kernel == 2 and nb % 32 == 0 and (N * esz) % 32 == 0 and 2 <= nb // 32 <= 32:
+        lpn = 2
+        while lpn < nb // 32:
+            lpn *= 2
+        return f"spmm_csr_wide<TagF32,{tag},{lpn},1>"
+    nvec = nb // 16
     if nvec <= 32:
         lpn = 2
         while lpn < nvec:
             lpn *= 2
-        return lpn, 1
-    return 32, 2 if nvec <= 64 else 4
+        return f"spmm_csr_persistent<TagF32,{tag},{lpn},1>"
+    return f"spmm_csr_persistent<TagF32,{tag},32,{2 if nvec <= 64 else 4}>"
 
 
 def measured_peaks():
@@ -289,6 +304,13 @@ def workload_label(args, N: int) -> str:
     return f"rmat-s{args.scale}-ef16-n{N}-fp32-grid{args.grid}"
 
 
+def workload_config(args, M, K, N, nnz) -> dict:
+    """The workload both arms run (the same keys and values in each arm's line)."""
+    return {"workload": workload_label(args, N), "M": M, "K": K, "N": N, "nnz": nnz,
+            "tile_grid": args.grid,
+            "l2": "inputs larger than L2 (A+B+C = %.2f GB per step)" % (min_bytes(M, K, N, nnz) / 1e9)}
+
+
 def run_reference(args):
     """The FP64 oracle on the host cores (rank 0 only)."""
     import torch
@@ -316,8 +338,7 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": flops_step / (value * 1e9) * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_label(args, args.n), "M": A.M, "K": A.K, "N": args.n,
-                   "nnz": A.nnz, "tile_grid": args.grid},
+        "config": workload_config(args, A.M, A.K, args.n, A.nnz),
         "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
                          "sample": desc},
         "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0,
@@ -347,7 +368,7 @@ def run_ours(args):
     M, K, N, nnz = A.M, A.K, args.n, A.nnz
     C = torch.empty(M, N, device=dev)
     tun = binding.make_tuning(chunk_items=args.chunk, warps_per_cta=args.warps,
-                              tile_order=args.order)
+                              tile_order=args.order, kernel=args.kernel)
     plan = binding.Plan(A.rowptr, M, K, nnz, N, TR, TC, tuning=tun)
     ws = binding.workspace(plan.workspace_bytes, dev)
     stream = torch.cuda.current_stream()
@@ -466,8 +487,22 @@ def run_ours(args):
                    "what": "cuSPARSE SpMM through torch.sparse.mm on the same A and B (context only)"}
         del At
 
+    # the metric's second half (BF16 vs FP32 at stated error) and the small
+    # workload, measured in the same run on rank 0
+    precision = small = None
+    if rank == 0 and not args.no_forms:
+        del B
+        torch.cuda.empty_cache()
+        precision = precision_results(A, dev, args.grid, max(5, min(args.steps, 20)),
+                                      max(3, args.warmup))
+        small = small_results(dev)
+        B = None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
+        if B is None:
+            from paper_2311_18141_gb300 import inputs
+            B = inputs.dense_normal(A.K, args.n, seed=2, device=dev)
         g, cores, desc, _ = cpu_oracle_sample(A, B, args.cpu_seconds)
         cpu = {"value": g, "unit": "GFLOP/s", "cores": cores, "kind": "oracle", "sample": desc}
 
@@ -478,24 +513,24 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": workload_label(args, N),
-                       "M": M, "K": K, "N": N, "nnz": nnz, "tile_grid": args.grid,
-                       "chunks": chunks, "work_units": units, "tile_order": args.order,
-                       "tile_nnz_max_over_avg": tile_nnz_imbalance(A.rowptr, M, TR),
-                       "parallelism": f"replicas x{world}" if world > 1 else "1 gpu",
-                       "l2": "inputs larger than L2 (A+B+C = %.2f GB per step)" % (algo_bytes / 1e9)},
+            "config": workload_config(args, M, K, N, nnz),
+            "parallelism": f"replicas x{world}" if world > 1 else "1 gpu",
+            "plan": {"chunks": chunks, "work_units": units, "tile_order": args.order,
+                     "tile_nnz_max_over_avg": tile_nnz_imbalance(A.rowptr, M, TR)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                          "peak_source": f"{peak_kind} (copy bandwidth)",
                          "algorithmic_bytes_per_launch": algo_bytes,
-                         "kernel": "spmm_csr_persistent<TagF32,TagF32,%d,%d>" % kernel_shape(N, TC),
+                         "kernel": kernel_name(N, TC, kernel=args.kernel),
                          "launch_ms": launch_ms, "launch_ms_min": min(per_launch),
                          "launch_ms_max": max(per_launch), "kernel_source_sha256_16": src_hash},
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": args.steps,
             "context": context,
+            "precision": precision,
+            "small": small,
             "trace": trace,
             "clocks": sampler.summary(),
         }
@@ -519,60 +554,173 @@ def _time_ms(fn, steps, warmup, stream):
     return e0.elapsed_time(e1) / steps
 
 
-def run_precision(args):
-    """FP16 A values; B of width 256 stored FP32, BF16 and E4M3 + per-row scales;
-    FP32 accumulation.  Time per storage format and error against the FP64
-    oracle on a sample of rows (max and RMS of |C - C64| / (|A||B|))."""
-    import numpy as np
+def sample_rows(rowptr, n_random: int, seed: int):
+    """Rows the error report samples: the 32 heaviest (split across many work
+    units), up to 256 empty ones, up to 512 of 17..1999 nonzeros, n_random
+    random rows, and the first/last rows and row-block edges."""
+    lens = np.diff(rowptr.astype(np.int64))
+    M = lens.size
+    rng = np.random.default_rng(seed)
+    heavy = np.argsort(lens)[-32:]
+    empty = np.flatnonzero(lens == 0)
+    empty = rng.choice(empty, min(256, empty.size), replace=False) if empty.size else empty
+    mid = np.flatnonzero((lens > 16) & (lens < 2000))
+    mid = rng.choice(mid, min(512, mid.size), replace=False) if mid.size else mid
+    rand = rng.choice(M, min(n_random, M), replace=False)
+    edges = np.array([0, M - 1, M // 16 - 1, M // 16, M // 2], dtype=np.int64)
+    return np.unique(np.concatenate([heavy, empty, mid, rand, edges]).astype(np.int64))
+
+
+def sub_problem(rp, ci, rows):
+    """The sampled rows of A as their own CSR over the columns they touch:
+    (rowptr, remapped colind, positions of their nonzeros in A, touched columns)."""
+    rp = rp.astype(np.int64)
+    lens = rp[rows + 1] - rp[rows]
+    pos = (np.concatenate([np.arange(rp[r], rp[r + 1]) for r in rows]) if lens.sum()
+           else np.zeros(0, np.int64))
+    cols, local = np.unique(ci[pos], return_inverse=True)
+    sub_rp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+    return sub_rp, local.astype(np.int32), pos, cols
+
+
+def precision_results(A, dev, grid: str, steps: int, warmup: int):
+    """The precision form at full size: FP16 A values; B of width 256 stored as
+    FP32, BF16 and E4M3 with per-row FP32 scales; FP32 accumulation.  For each
+    format: the time of one spmm_csr (CUDA events, mean over `steps` after
+    `warmup`), its HBM roofline fraction, and the error against the FP64 oracle
+    on sampled rows, normalised by |A||B|: against the product of the original
+    FP32 data (what the storage costs) and against the product of the stored,
+    dequantised inputs (what the kernel adds)."""
     import torch
     import oracle
-    from paper_2311_18141_gb300 import binding
-    dev = torch.device("cuda")
-    binding.load_library()
+    from paper_2311_18141_gb300 import binding, inputs
     N = 256
-    A, B = make_workload(args.scale, N, dev)
-    v16 = A.vals.to(torch.float16)
     M, K, nnz = A.M, A.K, A.nnz
-    TR, TC = (int(x) for x in args.grid.split("x"))
+    B = inputs.dense_normal(K, N, seed=2, device=dev)
+    v16 = A.vals.to(torch.float16)
+    TR, TC = (int(x) for x in grid.split("x"))
     stream = torch.cuda.current_stream()
-    rows = torch.arange(0, M, 97, device=dev)
-    rows_h = rows.cpu().numpy()
     rp, ci = A.rowptr.cpu().numpy(), A.colind.cpu().numpy()
-    v64 = v16.float().cpu().numpy().astype(np.float64)
-    Bh = B.cpu().numpy()
-    ref = oracle.spmm_rows(rp, ci, v64, Bh, rows_h)
-    bound = oracle.spmm_rows(rp, ci, np.abs(v64), np.abs(Bh.astype(np.float64)), rows_h)
+    rows = sample_rows(rp, 1000, seed=83)
+    sub_rp, sub_ci, pos, cols = sub_problem(rp, ci, rows)
+    v = oracle.decode_f16(v16.view(torch.int16).cpu().numpy().view(np.uint16)[pos])
+    cols_d = torch.from_numpy(cols).to(dev)
+    rows_d = torch.from_numpy(rows).to(dev)
+    b32 = B[cols_d].cpu().numpy().astype(np.float64)
+    ref0 = oracle.spmm(sub_rp, sub_ci, v, b32)
+    bound0 = oracle.abs_bound(sub_rp, sub_ci, v, b32)
     out = {}
+    plan = binding.Plan(A.rowptr, M, K, nnz, N, TR, TC)
+    ws = binding.workspace(plan.workspace_bytes, dev)
+    C = torch.empty(M, N, device=dev)
     for fmt in ("f32", "bf16", "e4m3"):
         scale = None
         if fmt == "f32":
-            Bq = B
+            Bq, bdq = B, b32
         elif fmt == "bf16":
             Bq = torch.empty(K, N, dtype=torch.bfloat16, device=dev)
             binding.spmm_quantize_rows(B, binding.SPMM_BF16, Bq)
+            bdq = oracle.decode_bf16(Bq[cols_d].view(torch.int16).cpu().numpy().view(np.uint16))
         else:
             Bq = torch.empty(K, N, dtype=torch.uint8, device=dev)
             scale = torch.empty(K, dtype=torch.float32, device=dev)
             binding.spmm_quantize_rows(B, binding.SPMM_E4M3, Bq, scale)
-        C = torch.empty(M, N, device=dev)
-        plan = binding.Plan(A.rowptr, M, K, nnz, N, TR, TC)
-        ws = binding.workspace(plan.workspace_bytes, dev)
+            bdq = oracle.dequantize_rows(Bq[cols_d].cpu().numpy(), scale[cols_d].cpu().numpy(),
+                                         "e4m3")
 
         def step():
             binding.spmm_csr(A.rowptr, A.colind, v16, Bq, C, M, K, N, nnz, b_scale=scale,
                              plan=plan, ws=ws, stream=stream)
-        ms = _time_ms(step, args.steps, args.warmup, stream)
+        ms = _time_ms(step, steps, warmup, stream)
+        assert binding.spmm_get_device_status(ws) == 0
         w_b = {"f32": 4, "bf16": 2, "e4m3": 1}[fmt]
         algo = min_bytes(M, K, N, nnz, w_val=2, w_b=w_b) + (4 * K if fmt == "e4m3" else 0)
-        got = C[rows].double().cpu().numpy()
-        rel = np.abs(got - ref) / np.maximum(bound, 1e-30)
+        got = C[rows_d].double().cpu().numpy()
+        rel0 = np.abs(got - ref0) / np.maximum(bound0, 1e-30)
+        ref1 = oracle.spmm(sub_rp, sub_ci, v, bdq)
+        bound1 = oracle.abs_bound(sub_rp, sub_ci, v, bdq)
+        rel1 = np.abs(got - ref1) / np.maximum(bound1, 1e-30)
         out[fmt] = {"ms": ms, "gflops": 2.0 * nnz * N / ms / 1e6,
+                    "kernel": kernel_name(N, TC, esz=w_b,
+                                          tag={"f32": "TagF32", "bf16": "TagBF16",
+                                               "e4m3": "TagE4M3"}[fmt]).replace(
+                                              "<TagF32,", "<TagF16,"),
+                    "algorithmic_bytes": algo,
                     "hbm_frac": algo / (ms * 1e-3) / 1e9 / measured_peaks()[0],
-                    "err_max": float(rel.max()), "err_rms": float(np.sqrt((rel ** 2).mean()))}
-        plan.close()
-    print(json.dumps({"workload": f"rmat-s{args.scale}-fp16A-n256", "tile_grid": args.grid,
-                      "nnz": nnz, "results": out, "error_sample_rows": int(rows.numel())}),
-          flush=True)
+                    "err_max": float(rel0.max()), "err_rms": float(np.sqrt((rel0 ** 2).mean())),
+                    "err_max_vs_stored_inputs": float(rel1.max())}
+        del Bq
+    plan.close()
+    return {"workload": f"rmat-s22-fp16A-n256-grid{grid}" if A.M == 1 << 22 else
+            f"rmat-fp16A-n256-grid{grid}", "N": N, "tile_grid": grid,
+            "error_sample_rows": int(rows.size), "error_unit": "|C - C64| / (|A||B|)",
+            "results": out,
+            "bf16_faster_than_f32": out["bf16"]["ms"] < out["f32"]["ms"],
+            "bf16_within_1e-2": out["bf16"]["err_max"] <= 1e-2,
+            "e4m3_faster_than_bf16": out["e4m3"]["ms"] < out["bf16"]["ms"]}
+
+
+def small_results(dev, steps: int = 200):
+    """The small FP32 form: A 4096 x 4096 with exactly 16 nonzeros per row, B
+    4096 x 32.  L2-resident and launch-bound, so times are per call: the
+    device time of back-to-back calls (CUDA events), the host time of the
+    spmm_csr call itself (no synchronisation), and the FP64 oracle on one
+    host core and on all of them."""
+    import torch
+    import oracle
+    from paper_2311_18141_gb300 import binding, inputs
+    A = inputs.uniform_csr(4096, 4096, 16, seed=1, device=dev)
+    N = 32
+    B = inputs.dense_normal(4096, N, seed=1, device=dev)
+    C = torch.empty(4096, N, device=dev)
+    plan = binding.Plan(A.rowptr, A.M, A.K, A.nnz, N, 1, 1)
+    ws = binding.workspace(plan.workspace_bytes, dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        binding.spmm_csr(A.rowptr, A.colind, A.vals, B, C, A.M, A.K, N, A.nnz, plan=plan,
+                         ws=ws, stream=stream)
+    dev_us = _time_ms(step, steps, 20, stream) * 1e3
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        step()
+    host_us = (time.perf_counter() - t0) * 1e6 / steps
+    torch.cuda.synchronize()
+    assert binding.spmm_get_device_status(ws) == 0
+    plan.close()
+    rp, ci, v, Bh = (A.rowptr.cpu().numpy(), A.colind.cpu().numpy(), A.vals.cpu().numpy(),
+                     B.cpu().numpy())
+
+    def oracle_us(threads):
+        oracle.set_threads(threads)
+        reps, t = 0, 0.0
+        while t < 1.0:
+            t0 = time.perf_counter()
+            oracle.spmm(rp, ci, v, Bh)
+            t += time.perf_counter() - t0
+            reps += 1
+        return t * 1e6 / reps
+
+    cores = len(os.sched_getaffinity(0))
+    one, allc = oracle_us(1), oracle_us(cores)
+    flops = 2.0 * A.nnz * N
+    return {"workload": "uniform-4096-16nnz-n32-fp32", "nnz": A.nnz, "N": N,
+            "device_us_per_call": dev_us, "gflops": flops / (dev_us * 1e-6) / 1e9,
+            "host_us_per_call": host_us,
+            "kernel": kernel_name(N, 1),
+            "cache": "L2-resident (1.6 MB), back-to-back calls",
+            "oracle_us_1_core": one, "oracle_us_all_cores": allc, "oracle_cores": cores}
+
+
+def run_precision(args):
+    """The precision form alone (see precision_results)."""
+    import torch
+    from paper_2311_18141_gb300 import binding
+    dev = torch.device("cuda")
+    binding.load_library()
+    A, _ = make_workload(args.scale, 8, dev)
+    print(json.dumps(precision_results(A, dev, args.grid, args.steps, args.warmup)), flush=True)
 
 
 def run_gcn(args):
@@ -728,6 +876,76 @@ def run_spgemm(args):
                       "min_bytes": bytes_min, "context": context}), flush=True)
 
 
+def run_gather(args):
+    """The SpMM's B gathers alone (spmm_bench_gather): for every nonzero of the
+    R-MAT scale-22 matrix and every column block, the block's segment of B row
+    colind[e], in the SpMM's interleaved order, nothing else.  Timed for the
+    benchmark's 16 x 4 grid (128-byte segments) and 16 x 1 (512 bytes), on the
+    matrix's own column stream, on uniform random columns (no reuse: DRAM
+    bound) and on columns below 60,000 (30 MB of B rows: L2-resident), next to
+    the full SpMM at the same grid.  The gathered bytes are nnz * N * 4."""
+    import torch
+    from paper_2311_18141_gb300 import binding
+    dev = torch.device("cuda")
+    binding.load_library()
+    A, B = make_workload(args.scale, args.n, dev)
+    M, K, N, nnz = A.M, A.K, args.n, A.nnz
+    stream = torch.cuda.current_stream()
+    out = torch.zeros(1, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    streams = {"rmat": A.colind,
+               "uniform": inputs_uniform_cols(nnz, K, 11, dev),
+               "l2_resident": inputs_uniform_cols(nnz, min(K, 60000), 12, dev)}
+    gathered = nnz * N * 4
+
+    def timed(fn, reps=5):
+        ts = []
+        for r in range(reps + 1):
+            flush.zero_()   # L2 starts cold for every rep
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if r:
+                ts.append(e0.elapsed_time(e1))
+        return sorted(ts)[len(ts) // 2]
+
+    res = {}
+    for grid in ("16x4", "16x1"):
+        TR, TC = (int(x) for x in grid.split("x"))
+        row = {}
+        for name, ci in streams.items():
+            ms = timed(lambda: binding.spmm_bench_gather(ci, nnz, B, K, N, TC, out,
+                                                         stream=stream))
+            row[name] = {"ms": ms, "gather_TBps": gathered / (ms * 1e-3) / 1e12}
+        C = torch.empty(M, N, device=dev)
+        plan = binding.Plan(A.rowptr, M, K, nnz, N, TR, TC,
+                            tuning=binding.make_tuning(tile_order=args.order))
+        ws = binding.workspace(plan.workspace_bytes, dev)
+        ms = timed(lambda: binding.spmm_csr(A.rowptr, A.colind, A.vals, B, C, M, K, N, nnz,
+                                            plan=plan, ws=ws, stream=stream))
+        row["spmm_ms"] = ms
+        row["spmm_over_gather_floor"] = ms / row["rmat"]["ms"]
+        row["spmm_hbm_frac_at_gather_floor"] = (min_bytes(M, K, N, nnz) /
+                                                (row["rmat"]["ms"] * 1e-3) / 1e9 /
+                                                measured_peaks()[0])
+        plan.close()
+        del C, ws
+        res[grid] = row
+    print(json.dumps({"workload": f"gather-rmat-s{args.scale}-n{N}", "nnz": nnz,
+                      "gathered_bytes": gathered, "results": res}), flush=True)
+
+
+def inputs_uniform_cols(nnz, K, seed, device):
+    """nnz column indices uniform in [0, K), from the counter-based generator."""
+    import torch
+    from paper_2311_18141_gb300 import inputs
+    h = inputs.hash_u32(torch.arange(nnz, dtype=torch.int64, device=device), seed,
+                        inputs.STREAM_COLS)
+    return (h % K).to(torch.int32)
+
+
 def run_loadsim(args):
     """Fig. 1's analysis on the host: R-MAT scale 17, edge factor 8, a = 0.6,
     b = c = d = 0.4/3, squared on a 16 x 16 grid -- end-to-end vs synchronised
@@ -740,9 +958,13 @@ def run_loadsim(args):
     out = {"workload": "loadsim-rmat-s17-ef8-a0.6-16x16", "nnz": A.nnz}
     for name, (r, c) in (("as_generated", (rp, ci)),
                          ("relabelled", loadsim.relabel(rp, ci, np.random.default_rng(0).permutation(A.M)))):
-        im = loadsim.imbalance(loadsim.spgemm_stage_work(r, c, r, c, A.K, A.K, 16))
+        w = loadsim.spgemm_stage_work(r, c, r, c, A.K, A.K, 16)
+        im = loadsim.imbalance(w)
+        ims = loadsim.imbalance(w, offset=True)
         out[name] = {"spgemm_end_to_end": im.end_to_end, "spgemm_synchronised": im.synchronised,
-                     "spgemm_worst_stage": float(im.per_stage.max())}
+                     "spgemm_worst_stage": float(im.per_stage.max()),
+                     "spgemm_synchronised_offset": ims.synchronised,
+                     "spgemm_worst_stage_offset": float(ims.per_stage.max())}
         for TR, TC in ((16, 4), (16, 1), (4, 4)):
             imm = loadsim.imbalance(loadsim.spmm_stage_work(r, c, A.K, 128, TR, TC, 16))
             out[name][f"spmm_{TR}x{TC}_end_to_end"] = imm.end_to_end
@@ -757,6 +979,9 @@ def main():
         return
     if args.workload == "spgemm":
         run_spgemm(args)
+        return
+    if args.workload == "gather":
+        run_gather(args)
         return
     if args.workload == "precision":
         run_precision(args)

@@ -85,8 +85,20 @@ typedef struct spmm_tuning {
                               bit 4: interleave -- one queue per tile row hands out the
                               same chunk of its tiles in turn (bit 3: all warps start
                               on tile row 0)                                           */
-    int32_t reserved[4];
+    int32_t kernel;        /* SPMM_KERNEL_AUTO (0): the library's choice, today the
+                              16-byte staged kernel (it measured faster everywhere);
+                              SPMM_KERNEL_STAGED (1): the staged kernel;
+                              SPMM_KERNEL_WIDE (2): the 32-byte-lane register-gather
+                              kernel, or SPMM_ERR_MISALIGNED when B, C, their strides
+                              or the column blocks are not whole 32-byte vectors of
+                              2..32 vectors per block                                   */
+    int32_t reserved[3];
 } spmm_tuning;
+
+/* spmm_tuning.kernel values */
+#define SPMM_KERNEL_AUTO 0
+#define SPMM_KERNEL_STAGED 1
+#define SPMM_KERNEL_WIDE 2
 
 /* Human-readable name of a status code (static storage). */
 const char* spmm_status_string(int status);
@@ -294,6 +306,19 @@ int spmm_csr_noalloc(const int32_t* A_rowptr, const int32_t* A_colind, const voi
                      float beta, void* stream);
 
 /*
+ * spmm_csr_noalloc_status -- the device status of spmm_csr_noalloc calls on
+ *   the current device.  Errors that device code finds during such a call (an
+ *   inconsistent plan, SPMM_ERR_INTERNAL; a bounded wait that ran out,
+ *   SPMM_ERR_TIMEOUT) land in the status word of the fixed array, which no
+ *   workspace pointer reaches.  This call synchronises `stream`, copies that
+ *   word into *status (host) and clears it, like spmm_get_device_status does
+ *   for a caller workspace.  Each spmm_csr_noalloc call clears the word when
+ *   it starts, so read it after the call whose result you check and before the
+ *   next one.  Allocates nothing.
+ */
+int spmm_csr_noalloc_status(int32_t* status, void* stream);
+
+/*
  * spmm_csr_validate -- check the CSR invariants listed above on the device.
  *   Writes SPMM_OK or SPMM_ERR_BAD_CSR into the workspace status word (the
  *   first 64 bytes of `workspace`, which must hold at least 64 bytes); read it
@@ -336,6 +361,33 @@ int spmm_spgemm(const int32_t* A_rowptr, const int32_t* A_colind, const float* A
 int spmm_spgemm_copy(const void* workspace, int64_t M, int64_t nnzA, int64_t products,
                      int64_t entries, int32_t* C_rowptr, int32_t* C_colind, float* C_vals,
                      void* stream);
+
+/*
+ * spmm_bench_gather -- measurement kernel: the B gathers of spmm_csr alone.
+ *   Section 4 counts B's bytes once in the local product and notes that B
+ *   values may have to be reloaded; a CSR product reads, for every nonzero e
+ *   and every column block j, the block's segment of B row A_colind[e].  This
+ *   call issues exactly those reads (32 bytes per lane, the interleaved order
+ *   of spmm_csr's default tile order: chunk c of column blocks 0..TC-1 in
+ *   turn) and nothing else -- no row pointers, values or C -- so its time is a
+ *   floor for a product that gathers a B segment per nonzero, and a profile of
+ *   it shows B's own L2 hit rate.
+ *   A_colind  device int32[nnz], entries in [0, K) (trusted, as in spmm_csr).
+ *   B         device, K x N of b_dtype, row stride ldb elements, 32-byte
+ *             aligned; N split into tile_cols equal blocks of 64..1024 bytes,
+ *             each a multiple of 32 bytes, and ldb*elem_size a multiple of 32
+ *             (else SPMM_ERR_MISALIGNED).
+ *   items_per_group  positions each lane group reads per chunk (4..4096, a
+ *             multiple of 4); ctas_per_sm 0 = as many as fit.
+ *   out       device float[1]: the sum of every value read, taken as FP32
+ *             words, is ADDED to it (float atomics, so the low bits vary run to
+ *             run).  It keeps the loads from being dropped; for F32 B it also
+ *             checks that they read the right rows.
+ *   Returns SPMM_ERR_INVALID_ARG for bad sizes or nnz >= 2^31 - 2^18.
+ */
+int spmm_bench_gather(const int32_t* A_colind, int64_t nnz, const void* B, int32_t b_dtype,
+                      int64_t ldb, int64_t K, int64_t N, int32_t tile_cols,
+                      int32_t items_per_group, int32_t ctas_per_sm, float* out, void* stream);
 
 /* Synchronise `stream`, then copy the device status word of `workspace` into
  * *status (host) and clear it. */

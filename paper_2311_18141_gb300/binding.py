@@ -36,7 +36,7 @@ EXPORTED = [
     "spmm_plan_workspace_size", "spmm_plan_units", "spmm_csr_workspace_size", "spmm_csr",
     "spmm_csr_validate", "spmm_get_device_status", "spmm_csr_transpose_workspace_size",
     "spmm_csr_transpose", "spmm_gather_values", "spmm_sddmm_csr", "spmm_quantize_rows",
-    "spmm_csr_noalloc", "spmm_batch_create", "spmm_batch_destroy", "spmm_batch_workspace_size",
+    "spmm_csr_noalloc", "spmm_csr_noalloc_status", "spmm_bench_gather", "spmm_batch_create", "spmm_batch_destroy", "spmm_batch_workspace_size",
     "spmm_batch_set_shapes", "spmm_batch_get_shapes", "spmm_csr_batched",
     "spmm_batch_graph_launch", "spmm_batch_autotune", "spmm_spgemm_analyze", "spmm_spgemm",
     "spmm_spgemm_copy", "spmm_host_pipe_create", "spmm_host_pipe_submit", "spmm_host_pipe_wait",
@@ -58,7 +58,11 @@ class SpmmError(RuntimeError):
 class spmm_tuning(ctypes.Structure):
     _fields_ = [("chunk_items", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("tile_order", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("kernel", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+
+
+# spmm_tuning.kernel
+SPMM_KERNEL_AUTO, SPMM_KERNEL_STAGED, SPMM_KERNEL_WIDE = 0, 1, 2
 
 
 class spmm_problem(ctypes.Structure):
@@ -131,6 +135,8 @@ def load_library(path: str | None = None):
         lib.spmm_host_pipe_destroy.argtypes = [vp]
         lib.spmm_csr_noalloc.argtypes = [vp, vp, vp, i32, vp, vp, i32, vp, i64, vp, i64, i64, i64,
                                          i64, i64, i32, i32, f32, vp]
+        lib.spmm_csr_noalloc_status.argtypes = [vp, vp]
+        lib.spmm_bench_gather.argtypes = [vp, i64, vp, i32, i64, i64, i64, i32, i32, i32, vp, vp]
         for name in EXPORTED:
             if name not in ("spmm_status_string",):
                 getattr(lib, name).restype = ctypes.c_int
@@ -171,10 +177,12 @@ def _stream(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
-def make_tuning(chunk_items=0, warps_per_cta=0, ctas_per_sm=0, tile_order=0) -> spmm_tuning:
+def make_tuning(chunk_items=0, warps_per_cta=0, ctas_per_sm=0, tile_order=0,
+                kernel=SPMM_KERNEL_AUTO) -> spmm_tuning:
     t = spmm_tuning()
     t.chunk_items, t.warps_per_cta = int(chunk_items), int(warps_per_cta)
     t.ctas_per_sm, t.tile_order = int(ctas_per_sm), int(tile_order)
+    t.kernel = int(kernel)
     return t
 
 
@@ -323,6 +331,25 @@ def spmm_csr_noalloc(rowptr, colind, vals, B, C, M, K, N, nnz, *, a_scale=None, 
         dtype_code(B.dtype), _ptr(b_scale), int(B.stride(0)), _ptr(C), int(C.stride(0)), int(M),
         int(K), int(N), int(nnz), int(tile_rows), int(tile_cols), float(beta), _stream(stream)),
         "spmm_csr_noalloc")
+
+
+def spmm_bench_gather(colind, nnz, B, K, N, tile_cols, out, *, items_per_group=64,
+                      ctas_per_sm=0, stream=None) -> None:
+    """The B gathers of spmm_csr alone (measurement kernel); adds the sum of all
+    values read to ``out[0]``."""
+    _check(load_library().spmm_bench_gather(
+        _ptr(colind), int(nnz), _ptr(B), dtype_code(B.dtype), int(B.stride(0)), int(K), int(N),
+        int(tile_cols), int(items_per_group), int(ctas_per_sm), _ptr(out), _stream(stream)),
+        "spmm_bench_gather")
+
+
+def spmm_csr_noalloc_status(stream=None) -> int:
+    """Read and clear the device status word of spmm_csr_noalloc's fixed array
+    on the current device (synchronises ``stream``)."""
+    st = ctypes.c_int32()
+    _check(load_library().spmm_csr_noalloc_status(ctypes.byref(st), _stream(stream)),
+           "spmm_csr_noalloc_status")
+    return int(st.value)
 
 
 def spmm_selftest_wait_timeout(ws, limit_cycles: int = 1 << 20, stream=None) -> None:

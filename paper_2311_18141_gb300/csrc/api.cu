@@ -1,4 +1,5 @@
 // C ABI entry points: argument checks, plans, workspace layout and dispatch.
+#include <atomic>
 #include <stdlib.h>
 #include <string.h>
 
@@ -25,9 +26,16 @@ struct spmm_plan_s {
 namespace spmm {
 
 int device_sm_count() {
+    // cached per device: the hot calls ask for it on every launch
+    static std::atomic<int> cache[kMaxDevices];
     int dev = 0, n = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+    if (dev >= 0 && dev < kMaxDevices) {
+        n = cache[dev].load(std::memory_order_relaxed);
+        if (n > 0) return n;
+    }
     if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 148;
+    if (dev >= 0 && dev < kMaxDevices) cache[dev].store(n, std::memory_order_relaxed);
     return n;
 }
 
@@ -65,6 +73,8 @@ void resolve_tuning(const spmm_tuning* in, spmm_tuning* out) {
     if (out->ctas_per_sm < 0) out->ctas_per_sm = 0;
     if (out->tile_order < 0 || out->tile_order > 31) out->tile_order = 0;
     if (out->chunk_items < 0) out->chunk_items = 0;
+    if (out->kernel < SPMM_KERNEL_AUTO || out->kernel > SPMM_KERNEL_WIDE)
+        out->kernel = SPMM_KERNEL_AUTO;
 }
 
 // Column-block width for N split in TC blocks of B type `dt`: ceil(N/TC)
@@ -91,6 +101,19 @@ bool pick_shape(int64_t nvec, int* lpn, int* vpl) {
     if (nvec <= 64) { *vpl = 2; return true; }
     if (nvec <= 128) { *vpl = 4; return true; }
     return false;
+}
+
+// Shape of the 32-byte-lane kernel for a column block of `bytes` bytes: lanes
+// per item and 32-byte vectors per lane.  Built for blocks of 2 to 32 whole
+// 32-byte vectors (64 bytes to 1 KB); others run the staged kernel.
+bool pick_wide_shape(int64_t bytes, int* lpn, int* nv) {
+    const int64_t nvec = bytes / 32;
+    if (bytes % 32 != 0 || nvec < 2 || nvec > 32) return false;
+    int l = 2;
+    while (l < nvec) l <<= 1;
+    *lpn = l;
+    *nv = 1;
+    return true;
 }
 
 int plan_view(spmm_plan plan, int64_t M, int64_t K, int64_t nnz, int64_t N, int32_t* TR,
@@ -167,7 +190,7 @@ int spmm_plan_create(spmm_plan* plan, const int32_t* A_rowptr, int64_t M, int64_
     resolve_tuning(tuning, &p->tuning);
     p->D = p->tuning.chunk_items > 0 ? p->tuning.chunk_items
                                     : plan_default_chunk(M, nnz, tile_cols, device_sm_count(),
-                                                         plan_default_groups(N, tile_cols));
+                                                         plan_default_groups_wide(N, tile_cols));
     p->tuning.chunk_items = p->D;
     p->cap = plan_chunk_cap(M, nnz, tile_rows, p->D);
     const size_t bytes = plan_array_bytes(tile_rows, p->cap);
@@ -235,7 +258,7 @@ int spmm_csr_workspace_size(int64_t M, int64_t nnz, int64_t N, int32_t tile_rows
     if (st) return st;
     (void)tuning;  // a call without a plan always uses the default tuning
     const int32_t D = plan_default_chunk(M, nnz, tile_cols, device_sm_count(),
-                                         plan_default_groups(N, tile_cols));
+                                         plan_default_groups_wide(N, tile_cols));
     const int64_t cap = plan_chunk_cap(M, nnz, tile_rows, D);
     *bytes = plan_array_bytes(tile_rows, cap) + scratch_layout(tile_rows, tile_cols, cap, N).total;
     return SPMM_OK;
@@ -267,8 +290,15 @@ int spmm_csr(const int32_t* A_rowptr, const int32_t* A_colind, const void* A_val
         return SPMM_ERR_MISALIGNED;
     const int64_t W = column_block_width(N, tile_cols, b_dtype);
     if (W == 0) return SPMM_ERR_INVALID_ARG;
+    // The 32-byte-lane kernel needs every B row segment and C row segment on
+    // 32-byte boundaries; otherwise the 16-byte staged kernel runs.
+    const bool wide_ok = (W * eb) % 32 == 0 && (N * eb) % 32 == 0 && (ldb * eb) % 32 == 0 &&
+                         (ldc * 4) % 32 == 0 && ((uintptr_t)C & 31u) == 0 &&
+                         (!B || ((uintptr_t)B & 31u) == 0);
     int lpn = 0, vpl = 0;
     if (!pick_shape(W / epv, &lpn, &vpl)) return SPMM_ERR_UNSUPPORTED;
+    int wlpn = 0, wnv = 0;
+    const bool wide_shape = wide_ok && pick_wide_shape(W * eb, &wlpn, &wnv);
     if (!workspace || ((uintptr_t)workspace & 255u)) return SPMM_ERR_WORKSPACE;
 
     cudaStream_t s = (cudaStream_t)stream;
@@ -287,7 +317,7 @@ int spmm_csr(const int32_t* A_rowptr, const int32_t* A_colind, const void* A_val
     } else {
         resolve_tuning(nullptr, &tun);
         RB = (int32_t)((M + TR - 1) / TR);
-        D = plan_default_chunk(M, nnz, TC, device_sm_count(), plan_default_groups(N, TC));
+        D = plan_default_chunk(M, nnz, TC, device_sm_count(), plan_default_groups_wide(N, TC));
         cap = plan_chunk_cap(M, nnz, TR, D);
         // layout [scratch: status, counters, slots][plan arrays]: the status
         // word stays at the start of the caller's workspace
@@ -324,9 +354,17 @@ int spmm_csr(const int32_t* A_rowptr, const int32_t* A_colind, const void* A_val
     o.ctas_per_sm = tun.ctas_per_sm;
     o.flags = tun.tile_order;
     o.units = cap * TC;
-    const LaunchFn fn = spmm_launcher(a_dtype, b_dtype);
-    if (!fn) return SPMM_ERR_UNSUPPORTED;
-    const cudaError_t e = fn(lpn, vpl, p, o, s);
+    if (tun.kernel == SPMM_KERNEL_WIDE && !wide_shape) return SPMM_ERR_MISALIGNED;
+    cudaError_t e;
+    if (tun.kernel == SPMM_KERNEL_WIDE && wide_shape) {
+        const WideLaunchFn fn = wide_launcher(a_dtype, b_dtype);
+        if (!fn) return SPMM_ERR_UNSUPPORTED;
+        e = fn(wlpn, wnv, p, o, s);
+    } else {
+        const LaunchFn fn = spmm_launcher(a_dtype, b_dtype);
+        if (!fn) return SPMM_ERR_UNSUPPORTED;
+        e = fn(lpn, vpl, p, o, s);
+    }
     return e == cudaSuccess ? SPMM_OK : SPMM_ERR_CUDA;
 }
 

@@ -7,8 +7,9 @@
 // global counter with atomicAdd (Algorithm 3's fetch-and-add, over the whole
 // batch): a warp
 // that finishes a small problem moves straight on to the next item of any
-// problem.  The host orders problems by decreasing work, so the largest are
-// reserved first.  Each warp copies the descriptor of the problem it is working
+// problem.  The host orders problems by width, then by decreasing work within a
+// width, so the warps of an SM mostly run one kernel shape and the largest
+// problems of a width are reserved first.  Each warp copies the descriptor of the problem it is working
 // on into its own slot of shared memory, then runs the same unit code as the
 // single-problem kernel, with the problem's lane-group shape chosen at run time
 // from five compiled shapes.

@@ -1,6 +1,8 @@
 // Launch helpers for the persistent SpMM kernel instantiations.
 #pragma once
 
+#include <atomic>
+
 #include "common.cuh"
 
 namespace spmm {
@@ -14,8 +16,14 @@ struct LaunchOpts {
 
 int device_sm_count();
 
+// Devices for which per-device launch facts are cached.
+constexpr int kMaxDevices = 64;
+
 using LaunchFn = cudaError_t (*)(int lpn, int vpl, const Problem& p, const LaunchOpts& o,
                                  cudaStream_t s);
+// 32-byte-lane kernel: lpn lanes per item, nv 32-byte vectors per lane.
+using WideLaunchFn = cudaError_t (*)(int lpn, int nv, const Problem& p, const LaunchOpts& o,
+                                     cudaStream_t s);
 
 struct BatchEntry;
 // Batched persistent launch: `ctas_per_sm` 0 = occupancy limit.
@@ -23,10 +31,58 @@ using BatchLaunchFn = cudaError_t (*)(const BatchEntry* table, const int64_t* it
                                       int count, char* ws, int* counter, int64_t max_items,
                                       int ctas_per_sm, cudaStream_t s);
 
+// Resident CTAs per SM of `kern` for `threads` threads and `smem` dynamic
+// shared bytes, found once per device, kernel and CTA size (the attribute set
+// and the occupancy query stay off the per-call path).  The first query on a
+// device raises the kernel's dynamic shared-memory limit to the device's
+// opt-in maximum, so every later launch shape fits under it.  0 on a CUDA
+// error.  cache[dev][0] holds 128-thread CTAs, [1] 256-thread ones, [2] is 1
+// once the attribute is set.
+template <class Kern>
+int cached_ctas_per_sm(Kern kern, int threads, size_t smem,
+                       std::atomic<int> (&cache)[kMaxDevices][3]) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 0;
+    const int slot = threads > 128 ? 1 : 0;
+    int per_sm = cache[dev][slot].load(std::memory_order_relaxed);
+    if (per_sm > 0) return per_sm;
+    if (cache[dev][2].load(std::memory_order_acquire) == 0) {
+        int optin = 0;
+        if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess)
+            return 0;
+        if (smem > (size_t)optin) return 0;
+        if (smem > 0 &&
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) !=
+                cudaSuccess)
+            return 0;
+        if (smem == 0)   // no shared memory: give the SM's whole L1/shared array to L1
+            cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
+        cache[dev][2].store(1, std::memory_order_release);
+    }
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess)
+        return 0;
+    if (per_sm < 1) per_sm = 1;
+    cache[dev][slot].store(per_sm, std::memory_order_relaxed);
+    return per_sm;
+}
+
+// Grid of a persistent launch: SMs x resident CTAs (capped by `ctas_per_sm`
+// when given), no more CTAs than there are warp units to hand out.
+inline int64_t persistent_grid(int per_sm, int ctas_per_sm, int64_t warp_units, int warps) {
+    if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
+    int64_t grid = (int64_t)device_sm_count() * per_sm;
+    const int64_t need = (warp_units + warps - 1) / warps;
+    if (grid > need) grid = need;
+    if (grid < 1) grid = 1;
+    return grid;
+}
+
 // One launcher per (A value type, B type); one translation unit each so the
 // build compiles them in parallel.
 #define SPMM_DECLARE_LAUNCHER(a, b)                                                           \
     cudaError_t launch_spmm_##a##_##b(int, int, const Problem&, const LaunchOpts&, cudaStream_t); \
+    cudaError_t launch_wide_##a##_##b(int, int, const Problem&, const LaunchOpts&, cudaStream_t); \
     cudaError_t launch_batched_##a##_##b(const BatchEntry*, const int64_t*, int, char*, int*,     \
                                          int64_t, int, cudaStream_t);
 SPMM_DECLARE_LAUNCHER(f32, f32) SPMM_DECLARE_LAUNCHER(f32, f16)
@@ -41,6 +97,7 @@ SPMM_DECLARE_LAUNCHER(e4m3, bf16) SPMM_DECLARE_LAUNCHER(e4m3, e4m3)
 
 // launchers for (a_dtype, b_dtype), both SPMM_F32 .. SPMM_E4M3
 LaunchFn spmm_launcher(int a_dtype, int b_dtype);
+WideLaunchFn wide_launcher(int a_dtype, int b_dtype);
 BatchLaunchFn batched_launcher(int a_dtype, int b_dtype);
 
 }  // namespace spmm

@@ -62,3 +62,12 @@ extern "C" int spmm_csr_noalloc(const int32_t* A_rowptr, const int32_t* A_colind
                     ldb, C, ldc, M, K, N, nnz, tile_rows, tile_cols, beta, nullptr, ws,
                     kStaticScratchBytes, stream);
 }
+
+extern "C" int spmm_csr_noalloc_status(int32_t* status, void* stream) {
+    if (!status) return SPMM_ERR_INVALID_ARG;
+    void* ws = nullptr;
+    const int st = static_scratch(&ws);
+    if (st != SPMM_OK) return st;
+    // the same read-and-clear as spmm_get_device_status, on the array's words
+    return spmm_get_device_status(ws, status, stream);
+}

@@ -126,6 +126,17 @@ int plan_default_groups(int64_t N, int32_t TC) {
     return 32 / lpn;
 }
 
+int plan_default_groups_wide(int64_t N, int32_t TC) {
+    if (TC < 1) TC = 1;
+    const int64_t w = ((N + TC - 1) / TC + 3) / 4 * 4;   // FP32 columns of a block
+    if ((w * 4) % 32 != 0 || (N * 4) % 32 != 0) return plan_default_groups(N, TC);
+    const int64_t nvec = w * 4 / 32;                     // 32-byte vectors of a block
+    if (nvec < 2 || nvec > 32) return plan_default_groups(N, TC);
+    int lpn = 2;
+    while (lpn < nvec) lpn <<= 1;
+    return 32 / lpn;
+}
+
 size_t plan_array_bytes(int32_t TR, int64_t cap) {
     size_t a = ((size_t)(TR + 1) * 4 + 255) / 256 * 256;
     size_t b = ((size_t)(cap + TR) * 4 + 255) / 256 * 256;

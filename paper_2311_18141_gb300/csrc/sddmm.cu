@@ -11,6 +11,7 @@
 #include <string.h>
 
 #include "api_internal.cuh"
+#include "launch.cuh"
 #include "plan.cuh"
 #include "spmm_kernel.cuh"
 
@@ -328,24 +329,15 @@ __global__ void __launch_bounds__(256, SPMM_SDDMM_MINBLOCKS) sddmm_persistent(co
     }
 }
 
-int device_sm_count();
-
 template <class Tag, int LPN, int VPL>
 static cudaError_t launch_sddmm_one(const SddmmProblem& s, int64_t units, cudaStream_t st) {
+    static std::atomic<int> cache[kMaxDevices][3];
     using K = KCfg<TagF32, Tag, LPN, VPL>;
     auto kern = sddmm_persistent<Tag, LPN, VPL>;
     const size_t smem = (size_t)8 * SCfg<K>::STAGE_BYTES;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 256, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    int64_t grid = (int64_t)device_sm_count() * per_sm;
-    const int64_t need = ((units + K::G - 1) / K::G + 7) / 8;
-    if (grid > need) grid = need;
-    if (grid < 1) grid = 1;
+    const int per_sm = cached_ctas_per_sm(kern, 256, smem, cache);
+    if (per_sm == 0) return cudaErrorInvalidValue;
+    const int64_t grid = persistent_grid(per_sm, 0, (units + K::G - 1) / K::G, 8);
     kern<<<(unsigned)grid, 256, smem, st>>>(s);
     return cudaGetLastError();
 }

@@ -33,6 +33,7 @@
 #include <limits.h>
 
 #include "common.cuh"
+#include "schedule.cuh"
 
 #ifndef SPMM_MINBLOCKS
 #define SPMM_MINBLOCKS 3   // resident 256-thread CTAs per SM the register budget targets
@@ -52,18 +53,6 @@
 #endif
 
 namespace spmm {
-
-// Launch flags of the persistent kernel.
-constexpr int kFlagOrderColumn = 1;   // steal along the tile column first
-constexpr int kFlagWarpHome = 2;      // stagger home tiles per warp instead of per CTA
-constexpr int kFlagSweep = 4;         // all CTAs start in column block 0, steal column-major:
-                                      // one column block's B rows are live in L2 at a time
-constexpr int kFlagLockstep = 8;      // all warps start on tile 0 and visit the tiles in the
-                                      // same order (row- or column-major by bit 0): one tile's
-                                      // B rows are live in L2 at a time
-constexpr int kFlagInterleave = 16;   // one queue per tile row handing out the same chunk of
-                                      // its TC tiles in turn: warps that reserve one after the
-                                      // other read the same A chunk and the same B rows
 
 template <typename TA_, typename TB_, int LPN_, int VPL_, int NBUF_ = SPMM_NBUF>
 struct KCfg {
@@ -604,105 +593,19 @@ __device__ __forceinline__ uint32_t warp_staging(int lane, uint32_t& bar0,
     return smem + (uint32_t)(warps * 16 + w * stage_bytes);
 }
 
-__device__ __forceinline__ long long globaltimer_ns() {
-    long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// The persistent kernel: each warp is an independent worker.  With a trace
-// buffer (p.trace), lane 0 of every warp records its start and end time, the
-// units it walked and how many of them came from outside its home tile (row).
+// The persistent kernel: each warp is an independent worker (see
+// persistent_schedule for the reservation order and the optional trace).
 template <class TA, class TB, int LPN, int VPL>
 __global__ void __launch_bounds__(256, (KCfg<TA, TB, LPN, VPL>::MINB))
 spmm_csr_persistent(const Problem p, int flags) {
     using K = KCfg<TA, TB, LPN, VPL>;
     const int lane = threadIdx.x & 31;
-    const int g = lane / K::LPN;
-    const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     uint32_t bar0 = 0, phases = 0;
     const uint32_t wbase = warp_staging<K>(lane, bar0);
-    if (p.trace && lane == 0 && warp < p.trace_max) p.trace[warp].t_start_ns = globaltimer_ns();
-    int units = 0, stolen = 0;
-    if (flags & kFlagInterleave) {
-        // ticket k of tile row i is chunk k / TC of tile (i, k % TC); the
-        // tile row's first counter is its queue
-        const int home_i = (flags & kFlagLockstep) ? 0 : (int)blockIdx.x % p.TR;
-        for (int step = 0; step < p.TR; ++step) {
-            int i = home_i + step;
-            if (i >= p.TR) i -= p.TR;
-            const int nsub = p.blk_base[i + 1] - p.blk_base[i];
-            const int total = (nsub + K::G - 1) / K::G * p.TC;
-            int* ctr = p.tile_ctr + i * p.TC;
-            if (total == 0 || ld_relaxed(ctr) >= total) continue;
-            while (true) {
-                int k = 0;
-                if (lane == 0) k = atomicAdd(ctr, 1);
-                k = __shfl_sync(kFull, k, 0);
-                if (k >= total) break;
-                const int c = k / p.TC;
-                const int j = k - c * p.TC;
-                const LaneCols<K::VPL> lc = lane_cols<K, K::VPL, K::LPN>(p, j, lane % K::LPN);
-                const int cs = c * K::G + g;
-                ++units;
-                stolen += step != 0;
-                if (!walk_unit<K>(p, i, j, cs < nsub ? cs : -1, lc, lane, wbase, bar0, phases))
-                    goto done;
-            }
-        }
-    } else {
-        const int T = p.TR * p.TC;
-        const bool sweep = (flags & kFlagSweep) != 0;
-        const int home = (flags & kFlagLockstep) ? 0
-                         : sweep ? (int)blockIdx.x % p.TR
-                                 : ((flags & kFlagWarpHome) ? warp : (int)blockIdx.x) % T;
-        for (int step = 0; step < T; ++step) {
-            int t = home + step;
-            if (t >= T) t -= T;
-            int i, j;
-            if (sweep || (flags & kFlagOrderColumn)) {
-                j = t / p.TR;
-                i = t - j * p.TR;
-            } else {
-                i = t / p.TC;
-                j = t - i * p.TC;
-            }
-            const int tid = i * p.TC + j;
-            const int nsub = p.blk_base[i + 1] - p.blk_base[i];
-            const int nun = (nsub + K::G - 1) / K::G;   // units: G sub-chunks each
-            if (nun == 0) continue;
-            if (ld_relaxed(p.tile_ctr + tid) >= nun) continue;
-            const LaneCols<K::VPL> lc = lane_cols<K, K::VPL, K::LPN>(p, j, lane % K::LPN);
-            while (true) {
-                int c = 0;
-                if (lane == 0) c = atomicAdd(p.tile_ctr + tid, 1);
-                c = __shfl_sync(kFull, c, 0);
-                if (c >= nun) break;
-                const int cs = c * K::G + g;
-                ++units;
-                stolen += step != 0;
-                if (!walk_unit<K>(p, i, j, cs < nsub ? cs : -1, lc, lane, wbase, bar0, phases))
-                    goto done;
-            }
-        }
-    }
-done:
-    if (p.trace && lane == 0 && warp < p.trace_max) {
-        // the home tile (row) of the walk above, recomputed
-        int home;
-        if (flags & kFlagLockstep) home = 0;
-        else if (flags & kFlagInterleave) home = (int)blockIdx.x % p.TR;
-        else if (flags & kFlagSweep) home = (int)blockIdx.x % p.TR;
-        else home = ((flags & kFlagWarpHome) ? warp : (int)blockIdx.x) % (p.TR * p.TC);
-        uint32_t smid;
-        asm("mov.u32 %0, %%smid;" : "=r"(smid));
-        spmm_trace_record* r = p.trace + warp;
-        r->t_end_ns = globaltimer_ns();
-        r->units = units;
-        r->stolen = stolen;
-        r->home = home;
-        r->smid = (int32_t)smid;
-    }
+    persistent_schedule<K::G>(p, flags, [&](int i, int j, int cs) {
+        const LaneCols<K::VPL> lc = lane_cols<K, K::VPL, K::LPN>(p, j, lane % K::LPN);
+        return walk_unit<K>(p, i, j, cs, lc, lane, wbase, bar0, phases);
+    });
 }
 
 }  // namespace spmm

@@ -1,0 +1,4 @@
+// 32-byte-lane SpMM kernels: A values F16, B F16.
+#include "spmm_launch_impl.cuh"
+
+SPMM_DEFINE_WIDE_LAUNCHER(f16, f16, TagF16, TagF16)

@@ -5,9 +5,12 @@ algorithm on a p x p process grid and compares two kinds of balance:
 
 * end to end -- the work of process (i, j) summed over all stages, max/avg over
   the p*p processes (processes that never synchronise);
-* per stage -- in stage k every process (i, j) multiplies A's tile (i, k) by
-  B's tile (k, j); if processes synchronise after every stage, the run takes
-  sum_k max_ij w(i,j,k) against an ideal sum_k avg_ij w(i,j,k).
+* per stage -- in stage k every process (i, j) multiplies A's tile (i, k') by
+  B's tile (k', j); if processes synchronise after every stage, the run takes
+  sum_k max_ij w(i,j,k') against an ideal sum_k avg_ij w(i,j,k').  With the
+  iteration offset of Section 3.3 (stationary C) process (i, j) takes
+  k' = (i + j + k) mod p in stage k, so the tiles multiplied in one stage come
+  from p different block columns; without it (SUMMA's lockstep) k' = k.
 
 The work of a tile product is its number of scalar products: for SpGEMM
 w(i,j,k) = sum over the columns l of block k of nnz(A[rows of block i, l]) *
@@ -83,8 +86,20 @@ class Imbalance:
     per_process: np.ndarray    # summed work of every process (the heat map)
 
 
-def imbalance(w: np.ndarray) -> Imbalance:
-    """Both load-imbalance figures of stage work w[k, i, j]."""
+def staggered(w: np.ndarray) -> np.ndarray:
+    """Stage work reordered by the iteration offset of Section 3.3: entry
+    [k, i, j] becomes the work process (i, j) does in stage k, which is its
+    product for block (i + j + k) mod s (s stages)."""
+    s, p, q = w.shape
+    ii, jj = np.meshgrid(np.arange(p), np.arange(q), indexing="ij")
+    return np.stack([w[(ii + jj + k) % s, ii, jj] for k in range(s)])
+
+
+def imbalance(w: np.ndarray, offset: bool = False) -> Imbalance:
+    """Both load-imbalance figures of stage work w[k, i, j]; with `offset`, the
+    stages follow the iteration offset (see staggered)."""
+    if offset:
+        w = staggered(w)
     total = w.sum(axis=0)
     avg = total.mean()
     e2e = float(total.max() / avg) if avg > 0 else 1.0

@@ -19,9 +19,25 @@ TOL_F32 = 1e-5
 TOL_LOWP = 1e-2
 
 
+# kernels a test can ask for (spmm_tuning.kernel): the 16-byte staged kernel, and
+# the 32-byte-lane kernel wherever B, C and the column blocks are whole 32-byte
+# vectors (elsewhere run_spmm asks for the library's default instead)
+KERNELS = [binding.SPMM_KERNEL_STAGED, binding.SPMM_KERNEL_WIDE]
+
+
+def wide_ok(N, TC, esz=4):
+    """Whether the 32-byte-lane kernel accepts N columns in TC blocks (dense,
+    aligned tensors)."""
+    epv = 16 // esz
+    w = -(-N // TC)
+    w = -(-w // epv) * epv
+    nb = w * esz
+    return nb % 32 == 0 and (N * esz) % 32 == 0 and 2 <= nb // 32 <= 32
+
+
 def run_spmm(A, B, N, *, tile_rows=1, tile_cols=1, beta=0.0, C0=None, chunk_items=0,
              warps_per_cta=0, tile_order=0, vals=None, a_scale=None, b_scale=None, plan=True,
-             Bdev=None):
+             Bdev=None, kernel=binding.SPMM_KERNEL_AUTO):
     """Run spmm_csr on the GPU; returns C (float32, on the host) and the status word."""
     Ad = A.to(DEV)
     v = (vals if vals is not None else A.vals).to(DEV)
@@ -30,8 +46,11 @@ def run_spmm(A, B, N, *, tile_rows=1, tile_cols=1, beta=0.0, C0=None, chunk_item
         C = C0.clone().to(DEV)
     else:
         C = torch.full((A.M, N), float("nan"), device=DEV)
+    esz = (Bdev.element_size() if Bdev is not None else 4)
+    if kernel == binding.SPMM_KERNEL_WIDE and not wide_ok(N, tile_cols, esz):
+        kernel = binding.SPMM_KERNEL_AUTO
     tun = binding.make_tuning(chunk_items=chunk_items, warps_per_cta=warps_per_cta,
-                              tile_order=tile_order)
+                              tile_order=tile_order, kernel=kernel)
     if plan:
         pl = binding.Plan(Ad.rowptr, A.M, A.K, A.nnz, N, tile_rows, tile_cols, tuning=tun)
         ws = binding.workspace(pl.workspace_bytes)

@@ -119,9 +119,11 @@ def test_e4m3_values_with_row_scale():
     assert_close_rel(C.numpy(), ref, bound, TOL_F32, "e4m3 vals + row scale")
 
 
-def test_bf16_beats_f32_bytes_at_stated_error():
-    """Report line for the precision workload at test size: BF16 and E4M3 storage
-    errors against FP64 (max and RMS, normalised by |A||B|)."""
+def test_storage_formats_error_against_fp64():
+    """The precision workload's error check at test size: FP32, BF16 and E4M3
+    storage of B (FP16 A values) against the FP64 product of the original data,
+    max and RMS normalised by |A||B|; BF16 within 1e-2, E4M3 within its stated
+    bound.  (Which format is faster is measured by bench.py, not here.)"""
     A = inputs.rmat_csr(12, 16, seed=37)
     N = 256
     B = inputs.dense_normal(A.K, N, seed=38)

@@ -13,7 +13,7 @@ import oracle
 from paper_2311_18141_gb300 import binding, inputs
 from paper_2311_18141_gb300.inputs import CSR
 
-from gpu_util import TOL_F32, assert_close_rel, run_spmm
+from gpu_util import KERNELS, TOL_F32, assert_close_rel, run_spmm
 
 pytestmark = pytest.mark.gpu
 
@@ -28,33 +28,37 @@ def ref_and_bound(A, B, vals=None, beta=0.0, C0=None):
     return ref, bound
 
 
-def test_uniform_4096_n32_full():
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_uniform_4096_n32_full(kernel):
     """4096 x 4096, exactly 16 nonzeros per row, B 4096 x 32 (the small FP32 workload)."""
     A = inputs.uniform_csr(4096, 4096, 16, seed=1)
     B = inputs.dense_normal(4096, 32, seed=1)
-    C, st = run_spmm(A, B, 32)
+    C, st = run_spmm(A, B, 32, kernel=kernel)
     assert st == 0
     ref, bound = ref_and_bound(A, B)
     assert_close_rel(C.numpy(), ref, bound, TOL_F32, "uniform 4096 N=32")
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("grid", [(1, 1), (16, 4), (3, 2), (7, 1), (1, 4)])
 @pytest.mark.parametrize("chunk", [0, 64, 333])
-def test_rmat_grids_and_chunks(grid, chunk):
+def test_rmat_grids_and_chunks(grid, chunk, kernel):
     A = inputs.rmat_csr(12, 16, seed=2)
     N = 64
     B = inputs.dense_normal(A.K, N, seed=3)
-    C, st = run_spmm(A, B, N, tile_rows=grid[0], tile_cols=grid[1], chunk_items=chunk)
+    C, st = run_spmm(A, B, N, tile_rows=grid[0], tile_cols=grid[1], chunk_items=chunk,
+                     kernel=kernel)
     assert st == 0
     ref, bound = ref_and_bound(A, B)
     assert_close_rel(C.numpy(), ref, bound, TOL_F32, f"rmat grid {grid} chunk {chunk}")
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("N", [4, 8, 16, 32, 64, 128, 256, 512])
-def test_widths(N):
+def test_widths(N, kernel):
     A = inputs.rmat_csr(11, 8, seed=4)
     B = inputs.dense_normal(A.K, N, seed=5)
-    C, st = run_spmm(A, B, N, chunk_items=96)
+    C, st = run_spmm(A, B, N, chunk_items=96, kernel=kernel)
     assert st == 0
     ref, bound = ref_and_bound(A, B)
     assert_close_rel(C.numpy(), ref, bound, TOL_F32, f"N={N}")
@@ -65,23 +69,26 @@ def test_widths(N):
                                   dict(warps_per_cta=4, tile_order=5), dict(tile_order=8),
                                   dict(tile_order=9), dict(tile_order=16), dict(tile_order=24),
                                   dict(warps_per_cta=4, tile_order=16)])
-def test_launch_options(opts):
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_launch_options(opts, kernel):
     A = inputs.rmat_csr(12, 8, seed=6)
     N = 32
     B = inputs.dense_normal(A.K, N, seed=7)
-    C, st = run_spmm(A, B, N, tile_rows=4, tile_cols=2, **opts)
+    C, st = run_spmm(A, B, N, tile_rows=4, tile_cols=2, kernel=kernel, **opts)
     assert st == 0
     ref, bound = ref_and_bound(A, B)
     assert_close_rel(C.numpy(), ref, bound, TOL_F32, str(opts))
 
 
-def test_beta_accumulate_and_scale():
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_beta_accumulate_and_scale(kernel):
     A = inputs.rmat_csr(11, 16, seed=8)
     N = 32
     B = inputs.dense_normal(A.K, N, seed=9)
     C0 = inputs.dense_normal(A.M, N, seed=10)
     for beta in (1.0, -0.5):
-        C, st = run_spmm(A, B, N, tile_rows=2, tile_cols=2, beta=beta, C0=C0, chunk_items=128)
+        C, st = run_spmm(A, B, N, tile_rows=2, tile_cols=2, beta=beta, C0=C0, chunk_items=128,
+                         kernel=kernel)
         assert st == 0
         ref, bound = ref_and_bound(A, B, beta=beta, C0=C0)
         assert_close_rel(C.numpy(), ref, bound, TOL_F32, f"beta={beta}")
@@ -95,7 +102,8 @@ def test_beta_zero_ignores_nan_in_c():
     assert st == 0 and not torch.isnan(C).any()
 
 
-def test_empty_rows_ragged_blocks_and_heavy_row():
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_empty_rows_ragged_blocks_and_heavy_row(kernel):
     # rows: many empty, one enormous row split across many chunks, ragged M
     M, K, N = 1001, 5000, 32
     rng = np.random.default_rng(13)
@@ -112,7 +120,8 @@ def test_empty_rows_ragged_blocks_and_heavy_row():
     B = inputs.dense_normal(K, N, seed=14)
     ref, bound = ref_and_bound(A, B)
     for grid, chunk in [((1, 1), 64), ((5, 2), 64), ((13, 4), 50), ((1, 1), 0)]:
-        C, st = run_spmm(A, B, N, tile_rows=grid[0], tile_cols=grid[1], chunk_items=chunk)
+        C, st = run_spmm(A, B, N, tile_rows=grid[0], tile_cols=grid[1], chunk_items=chunk,
+                         kernel=kernel)
         assert st == 0
         assert_close_rel(C.numpy(), ref, bound, TOL_F32, f"heavy grid {grid} chunk {chunk}")
         empty = lens == 0
@@ -173,13 +182,34 @@ def test_empty_matrix_and_degenerate_shapes():
     assert_close_rel(C.numpy(), ref, bound, TOL_F32, "tiny")
 
 
-def test_deterministic_bitwise():
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_deterministic_bitwise(kernel):
     A = inputs.rmat_csr(13, 16, seed=22)
     N = 128
     B = inputs.dense_normal(A.K, N, seed=23)
-    C1, _ = run_spmm(A, B, N, tile_rows=16, tile_cols=4, chunk_items=77)
-    C2, _ = run_spmm(A, B, N, tile_rows=16, tile_cols=4, chunk_items=77)
+    C1, _ = run_spmm(A, B, N, tile_rows=16, tile_cols=4, chunk_items=77, kernel=kernel)
+    C2, _ = run_spmm(A, B, N, tile_rows=16, tile_cols=4, chunk_items=77, kernel=kernel)
     assert torch.equal(C1, C2)
+
+
+def test_wide_kernel_rejects_16_byte_layouts():
+    """The 32-byte-lane kernel, asked for explicitly, refuses column blocks,
+    strides or pointers that are not whole 32-byte vectors (the default choice
+    then runs the staged kernel instead)."""
+    A = inputs.uniform_csr(64, 64, 4, seed=24)
+    Ad = A.to("cuda")
+    tun = binding.make_tuning(kernel=binding.SPMM_KERNEL_WIDE)
+    for N, TC, off in [(4, 1, 0), (12, 1, 0), (16, 4, 0), (16, 1, 4)]:
+        B = inputs.dense_normal(64, N, seed=25).cuda()
+        Cbuf = torch.zeros(64 * N + off, device="cuda")
+        C = Cbuf[off:].view(64, N)
+        plan = binding.Plan(Ad.rowptr, 64, 64, A.nnz, N, 2, TC, tuning=tun)
+        ws = binding.workspace(plan.workspace_bytes)
+        with pytest.raises(binding.SpmmError) as e:
+            binding.spmm_csr(Ad.rowptr, Ad.colind, Ad.vals, B, C, 64, 64, N, A.nnz, plan=plan,
+                             ws=ws)
+        assert e.value.status == binding.SPMM_ERR_MISALIGNED, (N, TC, off)
+        plan.close()
 
 
 def test_misaligned_and_plan_mismatch_rejected():
@@ -227,8 +257,9 @@ def test_validator():
     assert binding.spmm_get_device_status(ws) == 0
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("tile_order", [0, 9, 16])
-def test_every_unit_reserved_exactly_once_under_imbalance(tile_order):
+def test_every_unit_reserved_exactly_once_under_imbalance(tile_order, kernel):
     """Work reservation (Section 3.4): with one huge row and many empty ones on a
     16 x 4 grid, the result equals the oracle, so every chunk of every tile was
     processed exactly once (a missed unit leaves NaN, a doubled one doubles)."""
@@ -243,22 +274,27 @@ def test_every_unit_reserved_exactly_once_under_imbalance(tile_order):
     A = CSR(torch.from_numpy(rowptr.astype(np.int32)), torch.from_numpy(colind.astype(np.int32)),
             torch.ones(colind.size), M, K)
     B = torch.ones(K, N)
-    C, st = run_spmm(A, B, N, tile_rows=16, tile_cols=4, chunk_items=32, tile_order=tile_order)
+    C, st = run_spmm(A, B, N, tile_rows=16, tile_cols=4, chunk_items=32, tile_order=tile_order,
+                     kernel=kernel)
     assert st == 0
     assert torch.equal(C[:, 0], torch.from_numpy(lens.astype(np.float32)))
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("tile_order", [0, 16])
-def test_trace_records_account_for_every_unit(tile_order):
+def test_trace_records_account_for_every_unit(tile_order, kernel):
     """A traced launch computes the same C bit for bit; its per-warp records
     cover every work unit once (units of G = 32/LPN chunks per tile, summed over
     tiles), stolen units are a subset, times are ordered and SM ids valid."""
     A = inputs.rmat_csr(14, 16, seed=77)
     N, TR, TC = 128, 16, 4
+    # a column block is 32 FP32 values: 8 lanes of 16 bytes (G = 4 groups per
+    # warp) in the staged kernel, 4 lanes of 32 bytes (G = 8) in the wide one
+    G = 4 if kernel == binding.SPMM_KERNEL_STAGED else 8   # wide: N=128, TC=4 qualifies
     Ad = A.to("cuda")
     B = inputs.dense_normal(A.K, N, seed=78, device="cuda")
     plan = binding.Plan(Ad.rowptr, A.M, A.K, A.nnz, N, TR, TC,
-                        tuning=binding.make_tuning(tile_order=tile_order))
+                        tuning=binding.make_tuning(tile_order=tile_order, kernel=kernel))
     ws = binding.workspace(plan.workspace_bytes)
     C0 = torch.empty(A.M, N, device="cuda")
     binding.spmm_csr(Ad.rowptr, Ad.colind, Ad.vals, B, C0, A.M, A.K, N, A.nnz, plan=plan, ws=ws)
@@ -271,10 +307,10 @@ def test_trace_records_account_for_every_unit(tile_order):
     assert torch.equal(C0, C1)
     rec = binding.read_trace(buf)
     assert rec.size > 0
-    # units: per row block, ceil(chunks / G) units in each of the TC column blocks (G = 4 here)
+    # units: per row block, ceil(chunks / G) units in each of the TC column blocks
     chunks, _ = plan.units()
     total = int(rec["units"].sum())
-    assert chunks * TC / 4 <= total <= chunks * TC / 4 + TR * TC
+    assert chunks * TC / G <= total <= chunks * TC / G + TR * TC
     assert np.all(rec["stolen"] <= rec["units"]) and np.all(rec["stolen"] >= 0)
     assert np.all(rec["t_end_ns"] >= rec["t_start_ns"]) and np.all(rec["t_start_ns"] > 0)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
