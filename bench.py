@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--kernel", type=int, default=0,
                     help="spmm_tuning.kernel: 0 library default, 1 staged 16-byte kernel, "
                          "2 32-byte-lane kernel")
+    ap.add_argument("--lanes", type=int, default=0,
+                    help="spmm_tuning.lanes_per_item: 0 default, 2 or 4 lanes per column "
+                         "block of 4 or 8 vectors")
     ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
@@ -96,7 +99,7 @@ def stored_traffic(src_hash: str):
     return float(m_traffic.group(1))
 
 
-def kernel_name(N, TC, esz=4, kernel=0, tag="TagF32"):
+def kernel_name(N, TC, esz=4, kernel=0, tag="TagF32", lanes=0):
     """The persistent kernel the library launches for FP32 A and B of element
     size `esz` (aligned torch tensors, dense strides): the staged kernel by
     default, the 32-byte-lane kernel when asked for (kernel 2) and a column
@@ -115,6 +118,8 @@ def kernel_name(N, TC, esz=4, kernel=0, tag="TagF32"):
         lpn = 2
         while lpn < nvec:
             lpn *= 2
+        if lanes in (2, 4) and nvec in (4, 8) and lpn == nvec and lanes < nvec and nvec // lanes <= 4:
+            return f"spmm_csr_persistent<TagF32,{tag},{lanes},{nvec // lanes}>"
         return f"spmm_csr_persistent<TagF32,{tag},{lpn},1>"
     return f"spmm_csr_persistent<TagF32,{tag},32,{2 if nvec <= 64 else 4}>"
 
@@ -368,7 +373,8 @@ def run_ours(args):
     M, K, N, nnz = A.M, A.K, args.n, A.nnz
     C = torch.empty(M, N, device=dev)
     tun = binding.make_tuning(chunk_items=args.chunk, warps_per_cta=args.warps,
-                              tile_order=args.order, kernel=args.kernel)
+                              tile_order=args.order, kernel=args.kernel,
+                              lanes_per_item=args.lanes)
     plan = binding.Plan(A.rowptr, M, K, nnz, N, TR, TC, tuning=tun)
     ws = binding.workspace(plan.workspace_bytes, dev)
     stream = torch.cuda.current_stream()
@@ -522,7 +528,7 @@ def run_ours(args):
                          "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved / NOMINAL_HBM_GBS,
                          "peak_source": f"{peak_kind} (copy bandwidth)",
                          "algorithmic_bytes_per_launch": algo_bytes,
-                         "kernel": kernel_name(N, TC, kernel=args.kernel),
+                         "kernel": kernel_name(N, TC, kernel=args.kernel, lanes=args.lanes),
                          "launch_ms": launch_ms, "launch_ms_min": min(per_launch),
                          "launch_ms_max": max(per_launch), "kernel_source_sha256_16": src_hash},
             "cpu_baseline": cpu,

@@ -92,7 +92,11 @@ typedef struct spmm_tuning {
                               kernel, or SPMM_ERR_MISALIGNED when B, C, their strides
                               or the column blocks are not whole 32-byte vectors of
                               2..32 vectors per block                                   */
-    int32_t reserved[3];
+    int32_t lanes_per_item; /* 0: the default, one 16-byte vector per lane (a column
+                              block of 8 vectors is walked by 8 lanes); 2 or 4: a block
+                              of 4 or 8 vectors is walked by that many lanes holding
+                              several vectors each (staged kernel only)               */
+    int32_t reserved[2];
 } spmm_tuning;
 
 /* spmm_tuning.kernel values */

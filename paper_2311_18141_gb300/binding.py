@@ -58,7 +58,8 @@ class SpmmError(RuntimeError):
 class spmm_tuning(ctypes.Structure):
     _fields_ = [("chunk_items", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("tile_order", ctypes.c_int32),
-                ("kernel", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("kernel", ctypes.c_int32), ("lanes_per_item", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 # spmm_tuning.kernel
@@ -178,11 +179,11 @@ def _stream(stream=None):
 
 
 def make_tuning(chunk_items=0, warps_per_cta=0, ctas_per_sm=0, tile_order=0,
-                kernel=SPMM_KERNEL_AUTO) -> spmm_tuning:
+                kernel=SPMM_KERNEL_AUTO, lanes_per_item=0) -> spmm_tuning:
     t = spmm_tuning()
     t.chunk_items, t.warps_per_cta = int(chunk_items), int(warps_per_cta)
     t.ctas_per_sm, t.tile_order = int(ctas_per_sm), int(tile_order)
-    t.kernel = int(kernel)
+    t.kernel, t.lanes_per_item = int(kernel), int(lanes_per_item)
     return t
 
 

@@ -19,6 +19,7 @@ struct spmm_plan_s {
     int32_t* blk_base;
     int32_t* bnd_row;
     int32_t* bnd_nnz;
+    uint32_t* ends;       // row-end bitmap over the merge items
     spmm_trace_record* trace;   // caller-owned per-warp trace records (null: off)
     int32_t trace_max;
 };
@@ -75,6 +76,7 @@ void resolve_tuning(const spmm_tuning* in, spmm_tuning* out) {
     if (out->chunk_items < 0) out->chunk_items = 0;
     if (out->kernel < SPMM_KERNEL_AUTO || out->kernel > SPMM_KERNEL_WIDE)
         out->kernel = SPMM_KERNEL_AUTO;
+    if (out->lanes_per_item != 2 && out->lanes_per_item != 4) out->lanes_per_item = 0;
 }
 
 // Column-block width for N split in TC blocks of B type `dt`: ceil(N/TC)
@@ -113,6 +115,20 @@ bool pick_wide_shape(int64_t bytes, int* lpn, int* nv) {
     while (l < nvec) l <<= 1;
     *lpn = l;
     *nv = 1;
+    return true;
+}
+
+// The same with the lanes per item asked for by the tuning (2 or 4): a block
+// of 4 or 8 vectors can also be walked by fewer lanes holding 2 or 4 vectors
+// each (fewer instructions per byte, more registers per lane).  Other requests
+// keep the default shape.
+bool pick_shape_lanes(int64_t nvec, int32_t lanes, int* lpn, int* vpl) {
+    if (!pick_shape(nvec, lpn, vpl)) return false;
+    if ((lanes == 2 || lanes == 4) && *vpl == 1 && (nvec == 4 || nvec == 8) &&
+        *lpn == nvec && lanes < nvec && nvec / lanes <= 4) {
+        *vpl = (int)(nvec / lanes);
+        *lpn = lanes;
+    }
     return true;
 }
 
@@ -193,10 +209,14 @@ int spmm_plan_create(spmm_plan* plan, const int32_t* A_rowptr, int64_t M, int64_
                                                          plan_default_groups_wide(N, tile_cols));
     p->tuning.chunk_items = p->D;
     p->cap = plan_chunk_cap(M, nnz, tile_rows, p->D);
-    const size_t bytes = plan_array_bytes(tile_rows, p->cap);
+    const size_t arrays = plan_array_bytes(tile_rows, p->cap);
+    const size_t bytes = arrays + plan_ends_bytes(M + nnz);
     if (cudaMalloc(&p->mem, bytes) != cudaSuccess) { free(p); return SPMM_ERR_CUDA; }
     plan_carve(p->mem, tile_rows, p->cap, &p->blk_base, &p->bnd_row, &p->bnd_nnz);
-    cudaError_t e = plan_build(A_rowptr, M, p->TR, p->RB, p->D, p->cap, p->blk_base, p->bnd_row,
+    p->ends = reinterpret_cast<uint32_t*>(static_cast<char*>(p->mem) + arrays);
+    cudaError_t e = plan_build_ends(A_rowptr, M, M + nnz, p->ends, (cudaStream_t)stream);
+    if (e == cudaSuccess)
+        e = plan_build(A_rowptr, M, p->TR, p->RB, p->D, p->cap, p->blk_base, p->bnd_row,
                                p->bnd_nnz, (cudaStream_t)stream);
     if (e != cudaSuccess) { cudaFree(p->mem); free(p); return SPMM_ERR_CUDA; }
     *plan = p;
@@ -260,7 +280,8 @@ int spmm_csr_workspace_size(int64_t M, int64_t nnz, int64_t N, int32_t tile_rows
     const int32_t D = plan_default_chunk(M, nnz, tile_cols, device_sm_count(),
                                          plan_default_groups_wide(N, tile_cols));
     const int64_t cap = plan_chunk_cap(M, nnz, tile_rows, D);
-    *bytes = plan_array_bytes(tile_rows, cap) + scratch_layout(tile_rows, tile_cols, cap, N).total;
+    *bytes = plan_array_bytes(tile_rows, cap) + plan_ends_bytes(M + nnz) +
+             scratch_layout(tile_rows, tile_cols, cap, N).total;
     return SPMM_OK;
 }
 
@@ -297,6 +318,8 @@ int spmm_csr(const int32_t* A_rowptr, const int32_t* A_colind, const void* A_val
                          (!B || ((uintptr_t)B & 31u) == 0);
     int lpn = 0, vpl = 0;
     if (!pick_shape(W / epv, &lpn, &vpl)) return SPMM_ERR_UNSUPPORTED;
+    const int32_t lanes_req = plan ? plan->tuning.lanes_per_item : 0;
+    pick_shape_lanes(W / epv, lanes_req, &lpn, &vpl);
     int wlpn = 0, wnv = 0;
     const bool wide_shape = wide_ok && pick_wide_shape(W * eb, &wlpn, &wnv);
     if (!workspace || ((uintptr_t)workspace & 255u)) return SPMM_ERR_WORKSPACE;
@@ -306,6 +329,7 @@ int spmm_csr(const int32_t* A_rowptr, const int32_t* A_colind, const void* A_val
     int32_t TR = tile_rows, TC = tile_cols, RB, D;
     int64_t cap;
     int32_t *blk_base, *bnd_row, *bnd_nnz;
+    uint32_t* ends;
     spmm_tuning tun;
     if (plan) {
         if (plan->M != M || plan->nnz != nnz || plan->N != N || plan->TR != TR ||
@@ -313,6 +337,7 @@ int spmm_csr(const int32_t* A_rowptr, const int32_t* A_colind, const void* A_val
             return SPMM_ERR_PLAN_MISMATCH;
         RB = plan->RB; D = plan->D; cap = plan->cap;
         blk_base = plan->blk_base; bnd_row = plan->bnd_row; bnd_nnz = plan->bnd_nnz;
+        ends = plan->ends;
         tun = plan->tuning;
     } else {
         resolve_tuning(nullptr, &tun);
@@ -321,11 +346,14 @@ int spmm_csr(const int32_t* A_rowptr, const int32_t* A_colind, const void* A_val
         cap = plan_chunk_cap(M, nnz, TR, D);
         // layout [scratch: status, counters, slots][plan arrays]: the status
         // word stays at the start of the caller's workspace
-        const size_t pb = plan_array_bytes(TR, cap);
+        const size_t pa = plan_array_bytes(TR, cap);
+        const size_t pb = pa + plan_ends_bytes(M + nnz);
         const Scratch sc = scratch_layout(TR, TC, cap, N);
         if (workspace_bytes < pb + sc.total) return SPMM_ERR_WORKSPACE;
         plan_carve(ws + sc.total, TR, cap, &blk_base, &bnd_row, &bnd_nnz);
-        if (plan_build(A_rowptr, M, TR, RB, D, cap, blk_base, bnd_row, bnd_nnz, s) != cudaSuccess)
+        ends = reinterpret_cast<uint32_t*>(ws + sc.total + pa);
+        if (plan_build_ends(A_rowptr, M, M + nnz, ends, s) != cudaSuccess ||
+            plan_build(A_rowptr, M, TR, RB, D, cap, blk_base, bnd_row, bnd_nnz, s) != cudaSuccess)
             return SPMM_ERR_CUDA;
         workspace_bytes -= pb;
     }
@@ -338,7 +366,7 @@ int spmm_csr(const int32_t* A_rowptr, const int32_t* A_colind, const void* A_val
     p.B = B; p.b_scale = B_row_scale; p.C = C; p.ldb = ldb; p.ldc = ldc;
     p.M = (int32_t)M; p.N = (int32_t)N; p.a_dtype = a_dtype; p.beta = beta;
     p.TR = TR; p.TC = TC; p.RB = RB; p.W = (int32_t)W; p.D = D;
-    p.blk_base = blk_base; p.bnd_row = bnd_row; p.bnd_nnz = bnd_nnz;
+    p.blk_base = blk_base; p.bnd_row = bnd_row; p.bnd_nnz = bnd_nnz; p.ends = ends;
     p.status = reinterpret_cast<int32_t*>(ws);
     p.tile_ctr = reinterpret_cast<int32_t*>(ws + sc.counters_off);
     p.piece_cnt = p.tile_ctr + (size_t)TR * TC;

@@ -50,6 +50,15 @@ struct spmm_batch_s {
     size_t ws_needed = 0;                // for the current shapes
     size_t ws_bound = 0;                 // for any shapes the autotuner may pick
     int64_t max_items = 0;               // upper bound of work items
+    // device table order: products grouped by lane shape (one persistent launch
+    // per group), each group in execution order; exec[k] = index into probs
+    std::vector<int32_t> exec;
+    struct Group {
+        int32_t start, count, lpn;
+        int64_t max_items;
+    };
+    std::vector<Group> groups;
+    int32_t ctas_per_sm = 0;             // 0: occupancy limit (autotuned)
     cudaGraphExec_t graph = nullptr;
     const void* graph_ws = nullptr;
     cudaStream_t graph_stream = nullptr;
@@ -93,7 +102,7 @@ int batch_build(spmm_batch b, cudaStream_t s) {
         if (b->lpn[q] == 0) return SPMM_ERR_UNSUPPORTED;
         b->cap[q] = problem_cap(P, b->TR[q], b->D[q]);
         plan_off[q] = plan_total;
-        plan_total += plan_array_bytes(b->TR[q], b->cap[q]);
+        plan_total += plan_array_bytes(b->TR[q], b->cap[q]) + plan_ends_bytes(P.M + P.nnz);
         const size_t sc = problem_scratch(P, b->cap[q], b->TC[q]);
         piece_off[q] = (int64_t)ws;
         slot_off[q] = (int64_t)(ws + up256(4 * (size_t)b->cap[q] * b->TC[q]));
@@ -111,17 +120,35 @@ int batch_build(spmm_batch b, cudaStream_t s) {
         if (cudaMalloc(&b->plan_mem, plan_total) != cudaSuccess) return SPMM_ERR_CUDA;
         b->plan_bytes = plan_total;
     }
+    // group the device table by lane shape, widest items first; the stable
+    // sort keeps the execution order inside a group
+    b->exec.resize(n);
+    std::iota(b->exec.begin(), b->exec.end(), 0);
+    std::stable_sort(b->exec.begin(), b->exec.end(),
+                     [&](int x, int y) { return b->lpn[x] > b->lpn[y]; });
+    b->groups.clear();
+    for (int k = 0; k < n; ++k) {
+        const int q = b->exec[k];
+        if (b->groups.empty() || b->groups.back().lpn != b->lpn[q])
+            b->groups.push_back({k, 0, b->lpn[q], 0});
+        b->groups.back().count += 1;
+        b->groups.back().max_items += b->cap[q] * b->TC[q];
+    }
     b->h_table.assign(n, BatchEntry{});
-    for (int q = 0; q < n; ++q) {
+    for (int k = 0; k < n; ++k) {
+        const int q = b->exec[k];
         const spmm_problem& P = b->probs[q];
-        BatchEntry& e = b->h_table[q];
+        BatchEntry& e = b->h_table[k];
         memset(&e, 0, sizeof(e));
         Problem& p = e.p;
         int32_t *blk_base, *bnd_row, *bnd_nnz;
         plan_carve(static_cast<char*>(b->plan_mem) + plan_off[q], b->TR[q], b->cap[q], &blk_base,
                    &bnd_row, &bnd_nnz);
         const int32_t RB = (int32_t)std::max<int64_t>(1, (P.M + b->TR[q] - 1) / b->TR[q]);
-        if (plan_build(P.rowptr, P.M, b->TR[q], RB, b->D[q], b->cap[q], blk_base, bnd_row, bnd_nnz,
+        uint32_t* ends = reinterpret_cast<uint32_t*>(static_cast<char*>(b->plan_mem) + plan_off[q] +
+                                                     plan_array_bytes(b->TR[q], b->cap[q]));
+        if (plan_build_ends(P.rowptr, P.M, P.M + P.nnz, ends, s) != cudaSuccess ||
+            plan_build(P.rowptr, P.M, b->TR[q], RB, b->D[q], b->cap[q], blk_base, bnd_row, bnd_nnz,
                        s) != cudaSuccess)
             return SPMM_ERR_CUDA;
         p.rowptr = P.rowptr; p.colind = P.colind; p.vals = P.vals; p.a_scale = P.a_scale;
@@ -129,7 +156,7 @@ int batch_build(spmm_batch b, cudaStream_t s) {
         p.M = (int32_t)P.M; p.N = (int32_t)P.N; p.a_dtype = b->a_dtype; p.beta = P.beta;
         p.TR = b->TR[q]; p.TC = b->TC[q]; p.RB = RB;
         p.W = (int32_t)column_block_width(P.N, b->TC[q], b->b_dtype); p.D = b->D[q];
-        p.blk_base = blk_base; p.bnd_row = bnd_row; p.bnd_nnz = bnd_nnz;
+        p.blk_base = blk_base; p.bnd_row = bnd_row; p.bnd_nnz = bnd_nnz; p.ends = ends;
         e.piece_off = piece_off[q];
         e.slot_off = slot_off[q];
         e.lpn = b->lpn[q];
@@ -283,9 +310,15 @@ static int batch_enqueue(spmm_batch b, void* workspace, size_t bytes, cudaStream
         return SPMM_ERR_CUDA;
     const BatchLaunchFn fn = batched_launcher(b->a_dtype, b->b_dtype);
     if (!fn) return SPMM_ERR_UNSUPPORTED;
-    const cudaError_t e = fn(b->d_table, b->d_item_base, b->count, ws,
-                             reinterpret_cast<int*>(ws + kStatusBytes), b->max_items, 0, s);
-    return e == cudaSuccess ? SPMM_OK : SPMM_ERR_CUDA;
+    // one persistent launch per lane shape, each with its own work counter
+    int* counters = reinterpret_cast<int*>(ws + kStatusBytes);
+    for (size_t g = 0; g < b->groups.size(); ++g) {
+        const spmm_batch_s::Group& G = b->groups[g];
+        const cudaError_t e = fn(G.lpn, b->d_table + G.start, b->d_item_base + G.start, G.count,
+                                 ws, counters + g, G.max_items, b->ctas_per_sm, s);
+        if (e != cudaSuccess) return SPMM_ERR_CUDA;
+    }
+    return SPMM_OK;
 }
 
 int spmm_csr_batched(spmm_batch b, void* workspace, size_t workspace_bytes, void* stream) {

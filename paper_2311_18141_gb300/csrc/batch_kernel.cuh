@@ -1,30 +1,27 @@
-// Batched persistent SpMM: many independent products C_p = beta_p*C_p + A_p*B_p
-// in one launch.
+// Batched persistent SpMM: many independent products C_p = beta_p*C_p + A_p*B_p.
 //
-// Every problem keeps its own merge-path plan.  Its work units (G consecutive
-// sub-chunks, column block) are numbered after those of the problems before it
-// (item_base), and the warps of one persistent grid reserve items from a single
-// global counter with atomicAdd (Algorithm 3's fetch-and-add, over the whole
-// batch): a warp
-// that finishes a small problem moves straight on to the next item of any
-// problem.  The host orders problems by width, then by decreasing work within a
-// width, so the warps of an SM mostly run one kernel shape and the largest
-// problems of a width are reserved first.  Each warp copies the descriptor of the problem it is working
-// on into its own slot of shared memory, then runs the same unit code as the
-// single-problem kernel, with the problem's lane-group shape chosen at run time
-// from five compiled shapes.
+// Every product keeps its own merge-path plan.  Its work units (G consecutive
+// sub-chunks, column block) are numbered after those of the products before it
+// (item_base).  The products are grouped by lane shape (lanes per column
+// block), and each group runs as one persistent launch of the kernel compiled
+// for that shape: its warps reserve items from the group's counter with
+// atomicAdd (Algorithm 3's fetch-and-add, over the group's products), so a
+// warp that finishes a small product moves straight on to the next item of
+// any other.  Within a group the host orders products by width, then by
+// decreasing work, so the largest are reserved first.  Each warp copies the
+// descriptor of the product it is working on into its own slot of shared
+// memory and runs the same unit code as the single-product kernel.  One shape
+// per kernel keeps its register count, and so its resident warps, those of the
+// single-product kernel.
 #pragma once
 
 #include "spmm_kernel.cuh"
 
 #ifndef SPMM_BATCH_MINBLOCKS
-#define SPMM_BATCH_MINBLOCKS 2   // resident 256-thread CTAs per SM the register budget targets
+#define SPMM_BATCH_MINBLOCKS 3   // resident 256-thread CTAs per SM the register budget targets
 #endif
 #ifndef SPMM_BATCH_NBUF
 #define SPMM_BATCH_NBUF 2   // stage buffers per warp of the batched kernel
-#endif
-#ifndef SPMM_BATCH_UNIT_INLINE
-#define SPMM_BATCH_UNIT_INLINE __forceinline__   // or __noinline__: one function per shape
 #endif
 
 namespace spmm {
@@ -43,22 +40,17 @@ static_assert(sizeof(BatchEntry) % 4 == 0, "descriptor copied as 32-bit words");
 
 constexpr int kBatchWarps = 8;
 
-// Staging bytes per warp: the largest of the five shapes (VPL = 1; the
-// shapes with LPN < 8 stage whole 8-item batches).
-template <class TA, class TB>
+// Staging bytes per warp of the kernel for lane shape LPN.
+template <class TA, class TB, int LPN>
 __host__ __device__ constexpr int batch_stage_bytes() {
-    return KCfg<TA, TB, 32, 1, SPMM_BATCH_NBUF>::STAGE_BYTES >
-                   KCfg<TA, TB, 2, 1, SPMM_BATCH_NBUF>::STAGE_BYTES
-               ? KCfg<TA, TB, 32, 1, SPMM_BATCH_NBUF>::STAGE_BYTES
-               : KCfg<TA, TB, 2, 1, SPMM_BATCH_NBUF>::STAGE_BYTES;
+    return KCfg<TA, TB, LPN, 1, SPMM_BATCH_NBUF>::STAGE_BYTES;
 }
 
 // Unit u of a problem in column block j: its sub-chunks u*G .. u*G+G-1, counted
 // over all row blocks, one per lane group; each group finds its own row block.
 template <class TA, class TB, int LPN>
-__device__ SPMM_BATCH_UNIT_INLINE bool batch_unit(const Problem& p, int u, int j, int lane,
-                                                  uint32_t wbase, uint32_t bar0,
-                                                  uint32_t& phases) {
+__device__ __forceinline__ bool batch_unit(const Problem& p, int u, int j, int lane,
+                                           uint32_t wbase, uint32_t bar0, uint32_t& phases) {
     using K = KCfg<TA, TB, LPN, 1, SPMM_BATCH_NBUF>;
     const LaneCols<K::VPL> lc = lane_cols<K, K::VPL, K::LPN>(p, j, lane % K::LPN);
     const int gsc = u * K::G + lane / K::LPN;
@@ -75,29 +67,35 @@ __device__ SPMM_BATCH_UNIT_INLINE bool batch_unit(const Problem& p, int u, int j
     return walk_unit<K>(p, il, j, cs, lc, lane, wbase, bar0, phases);
 }
 
-template <class TA, class TB>
+// The products of one lane shape (LPN lanes per column block) of a batch:
+// table[0 .. count) with item_base[0 .. count] (the batch-wide prefix of
+// their work items, so item_base[0] need not be 0).  Warps reserve items
+// from `counter` and walk units of whichever product owns them.
+template <class TA, class TB, int LPN>
 __global__ void __launch_bounds__(kBatchWarps * 32, SPMM_BATCH_MINBLOCKS)
 spmm_csr_batched_kernel(const BatchEntry* __restrict__ table,
                         const int64_t* __restrict__ item_base, int count, char* ws,
                         int* counter) {
+    using K = KCfg<TA, TB, LPN, 1, SPMM_BATCH_NBUF>;
     __shared__ Problem sp[kBatchWarps];
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
     uint32_t bar0 = 0, phases = 0;
-    const uint32_t wbase =
-        warp_staging<KCfg<TA, TB, 32, 1, SPMM_BATCH_NBUF>>(lane, bar0, batch_stage_bytes<TA, TB>());
-    const int64_t total = item_base[count];
-    int cur = -1;   // problem whose descriptor is in sp[w]
+    const uint32_t wbase = warp_staging<K>(lane, bar0);
+    const int64_t first = item_base[0];
+    const int64_t total = item_base[count] - first;
+    int cur = -1;   // product whose descriptor is in sp[w]
     while (true) {
         int item = 0;
         if (lane == 0) item = atomicAdd(counter, 1);
         item = __shfl_sync(kFull, item, 0);
         if ((int64_t)item >= total) break;
-        // problem owning the item: largest q with item_base[q] <= item
+        const int64_t abs_item = first + item;
+        // product owning the item: largest q with item_base[q] <= abs_item
         int lo = 0, hi = count - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (item_base[mid] <= (int64_t)item) lo = mid;
+            if (item_base[mid] <= abs_item) lo = mid;
             else hi = mid - 1;
         }
         const BatchEntry* e = table + lo;
@@ -116,18 +114,10 @@ spmm_csr_batched_kernel(const BatchEntry* __restrict__ table,
             cur = lo;
         }
         const Problem& p = sp[w];
-        const int local = item - (int)item_base[lo];
+        const int local = (int)(abs_item - item_base[lo]);
         const int u = local / p.TC;
         const int j = local - u * p.TC;
-        bool ok;
-        switch (e->lpn) {
-            case 2: ok = batch_unit<TA, TB, 2>(p, u, j, lane, wbase, bar0, phases); break;
-            case 4: ok = batch_unit<TA, TB, 4>(p, u, j, lane, wbase, bar0, phases); break;
-            case 8: ok = batch_unit<TA, TB, 8>(p, u, j, lane, wbase, bar0, phases); break;
-            case 16: ok = batch_unit<TA, TB, 16>(p, u, j, lane, wbase, bar0, phases); break;
-            default: ok = batch_unit<TA, TB, 32>(p, u, j, lane, wbase, bar0, phases); break;
-        }
-        if (!ok) return;
+        if (!batch_unit<TA, TB, LPN>(p, u, j, lane, wbase, bar0, phases)) return;
     }
 }
 

@@ -54,6 +54,46 @@ __device__ __forceinline__ void cp_async16(uint32_t smem_addr, const void* gptr,
                  :: "r"(smem_addr), "l"(gptr), "r"(src_bytes) : "memory");
 #endif
 }
+// The same copy with a predicate instead of a size: `skip` writes 16 zero
+// bytes and reads nothing.
+__device__ __forceinline__ void cp_async16_zero_if(uint32_t smem_addr, const void* gptr,
+                                                   bool skip) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t"
+#if SPMM_CP_ASYNC_CA
+                 "cp.async.ca.shared.global [%0], [%1], 16, q;\n\t}"
+#else
+                 "cp.async.cg.shared.global [%0], [%1], 16, q;\n\t}"
+#endif
+                 :: "r"(smem_addr), "l"(gptr), "r"((int)skip) : "memory");
+}
+// L2 eviction priority for B gathers (SPMM_B_L2_HINT): 0 none; 1 evict_last
+// (B rows outrank the streaming A and C lines); 2 evict_first.  The policy
+// word is created by createpolicy in the thread that uses it (a cache-policy
+// operand must come from createpolicy; its encoding is opaque) and passed as
+// the last operand of cp.async, after the ignore-src predicate.
+#ifndef SPMM_B_L2_HINT
+#define SPMM_B_L2_HINT 0
+#endif
+__device__ __forceinline__ uint64_t b_gather_policy() {
+    uint64_t pol = 0;
+#if SPMM_B_L2_HINT == 1
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0;" : "=l"(pol));
+#elif SPMM_B_L2_HINT == 2
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0;" : "=l"(pol));
+#endif
+    return pol;
+}
+__device__ __forceinline__ void cp_async16_zero_if_hint(uint32_t smem_addr, const void* gptr,
+                                                        bool skip, uint64_t pol) {
+#if SPMM_B_L2_HINT
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t"
+                 "cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, q, %3;\n\t}"
+                 :: "r"(smem_addr), "l"(gptr), "r"((int)skip), "l"(pol) : "memory");
+#else
+    (void)pol;
+    cp_async16_zero_if(smem_addr, gptr, skip);
+#endif
+}
 __device__ __forceinline__ void cp_async_commit() {
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
@@ -320,6 +360,7 @@ struct Problem {
     const int32_t* blk_base;  // [TR+1] chunk prefix per row block
     const int32_t* bnd_row;   // boundary (row, nnz) at index blk_base[i] + i + c
     const int32_t* bnd_nnz;
+    const uint32_t* ends;     // row-end bitmap over the merge items (see plan_ends_bytes)
     // per-call scratch
     int32_t* tile_ctr;        // [TR*TC]
     int32_t* piece_cnt;       // [chunks*TC]

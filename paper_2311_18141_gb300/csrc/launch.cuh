@@ -26,8 +26,9 @@ using WideLaunchFn = cudaError_t (*)(int lpn, int nv, const Problem& p, const La
                                      cudaStream_t s);
 
 struct BatchEntry;
-// Batched persistent launch: `ctas_per_sm` 0 = occupancy limit.
-using BatchLaunchFn = cudaError_t (*)(const BatchEntry* table, const int64_t* item_base,
+// Batched persistent launch of the products table[0 .. count) of lane shape
+// `lpn`: `ctas_per_sm` 0 = occupancy limit.
+using BatchLaunchFn = cudaError_t (*)(int lpn, const BatchEntry* table, const int64_t* item_base,
                                       int count, char* ws, int* counter, int64_t max_items,
                                       int ctas_per_sm, cudaStream_t s);
 
@@ -35,7 +36,8 @@ using BatchLaunchFn = cudaError_t (*)(const BatchEntry* table, const int64_t* it
 // shared bytes, found once per device, kernel and CTA size (the attribute set
 // and the occupancy query stay off the per-call path).  The first query on a
 // device raises the kernel's dynamic shared-memory limit to the device's
-// opt-in maximum, so every later launch shape fits under it.  0 on a CUDA
+// opt-in maximum less its static shared memory, so every later launch shape
+// fits under it.  0 on a CUDA
 // error.  cache[dev][0] holds 128-thread CTAs, [1] 256-thread ones, [2] is 1
 // once the attribute is set.
 template <class Kern>
@@ -51,9 +53,13 @@ int cached_ctas_per_sm(Kern kern, int threads, size_t smem,
         if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
             cudaSuccess)
             return 0;
-        if (smem > (size_t)optin) return 0;
+        // the limit covers dynamic bytes only: static shared memory counts against it
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) return 0;
+        const int dyn_max = optin - (int)fa.sharedSizeBytes;
+        if (dyn_max < 0 || smem > (size_t)dyn_max) return 0;
         if (smem > 0 &&
-            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) !=
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max) !=
                 cudaSuccess)
             return 0;
         if (smem == 0)   // no shared memory: give the SM's whole L1/shared array to L1
@@ -83,8 +89,8 @@ inline int64_t persistent_grid(int per_sm, int ctas_per_sm, int64_t warp_units, 
 #define SPMM_DECLARE_LAUNCHER(a, b)                                                           \
     cudaError_t launch_spmm_##a##_##b(int, int, const Problem&, const LaunchOpts&, cudaStream_t); \
     cudaError_t launch_wide_##a##_##b(int, int, const Problem&, const LaunchOpts&, cudaStream_t); \
-    cudaError_t launch_batched_##a##_##b(const BatchEntry*, const int64_t*, int, char*, int*,     \
-                                         int64_t, int, cudaStream_t);
+    cudaError_t launch_batched_##a##_##b(int, const BatchEntry*, const int64_t*, int, char*,      \
+                                         int*, int64_t, int, cudaStream_t);
 SPMM_DECLARE_LAUNCHER(f32, f32) SPMM_DECLARE_LAUNCHER(f32, f16)
 SPMM_DECLARE_LAUNCHER(f32, bf16) SPMM_DECLARE_LAUNCHER(f32, e4m3)
 SPMM_DECLARE_LAUNCHER(f16, f32) SPMM_DECLARE_LAUNCHER(f16, f16)

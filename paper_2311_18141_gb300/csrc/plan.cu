@@ -100,7 +100,28 @@ __global__ void plan_bounds_kernel(const int32_t* __restrict__ rowptr, int M, in
     bnd_nnz[b] = (int32_t)(nnz_lo + y);
 }
 
+// One thread per row: set the bit of the row's end item.
+__global__ void plan_ends_kernel(const int32_t* __restrict__ rowptr, int M,
+                                 uint32_t* __restrict__ ends) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= M) return;
+    const int64_t item = (int64_t)r + rowptr[r + 1];
+    atomicOr(ends + (item >> 5), 1u << (item & 31));
+}
+
 static int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+size_t plan_ends_bytes(int64_t items) {
+    return ((size_t)(ceil_div(items, 32) + 2) * 4 + 255) / 256 * 256;
+}
+
+cudaError_t plan_build_ends(const int32_t* rowptr, int64_t M, int64_t items, uint32_t* ends,
+                            cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(ends, 0, plan_ends_bytes(items), s);
+    if (e != cudaSuccess || M == 0) return e;
+    plan_ends_kernel<<<(unsigned)ceil_div(M, 256), 256, 0, s>>>(rowptr, (int)M, ends);
+    return cudaGetLastError();
+}
 
 int64_t plan_chunk_cap(int64_t M, int64_t nnz, int32_t TR, int32_t D) {
     return ceil_div(M + nnz, D) + TR;

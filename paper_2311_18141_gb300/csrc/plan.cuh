@@ -21,6 +21,14 @@ size_t plan_array_bytes(int32_t TR, int64_t cap);
 // Split a plan-array region into its three arrays.
 void plan_carve(void* base, int32_t TR, int64_t cap, int32_t** blk_base, int32_t** bnd_row,
                 int32_t** bnd_nnz);
+// Row-end bitmap over the merge path of the whole matrix: the merge item of
+// row r's end is r + rowptr[r+1] (the item of nonzero e of row r is r + e),
+// and bit (r + rowptr[r+1]) is set for every row.  Bytes for M + nnz items
+// (two words of padding, so a 64-bit window read never leaves the array).
+size_t plan_ends_bytes(int64_t items);
+// Clear the bitmap and set the row ends (enqueued on `s`).
+cudaError_t plan_build_ends(const int32_t* rowptr, int64_t M, int64_t items, uint32_t* ends,
+                            cudaStream_t s);
 // Enqueue the two plan kernels on `s`.
 cudaError_t plan_build(const int32_t* rowptr, int64_t M, int32_t TR, int32_t RB, int32_t D,
                        int64_t cap, int32_t* blk_base, int32_t* bnd_row, int32_t* bnd_nnz,

@@ -47,6 +47,12 @@
 #ifndef SPMM_STAGE_ITEMS
 #define SPMM_STAGE_ITEMS 8 // items per lane group in one stage (of one 16-byte vector each)
 #endif
+#ifndef SPMM_RING
+#define SPMM_RING 0        // item slots of the per-item cp.async ring (0: stage buffers)
+#endif
+#ifndef SPMM_ENDS_BITMAP
+#define SPMM_ENDS_BITMAP 1 // 1: row ends from the plan's bitmap; 0: from row pointers
+#endif
 #ifndef SPMM_TMA
 #define SPMM_TMA 0         // 1: stage B rows with bulk copies on the TMA engine instead of
                            // per-lane cp.async (correct, but slower for 128-512 byte rows)
@@ -66,7 +72,9 @@ struct KCfg {
     static constexpr int ESZ = 16 / EPV;                       // bytes per B element
     // items decoded per group at a time (one bit each in a 32-bit mask), and
     // how many of them each lane of the group holds
-    static constexpr int MB = LPN < 8 ? 8 : LPN;
+    // (a lane holding VPL > 1 vectors takes MB = max(LPN, 8 / VPL) items, so a
+    // stage of one batch stays 8 vectors per lane)
+    static constexpr int MB = LPN >= 8 ? LPN : VPL == 1 ? 8 : (LPN > 8 / VPL ? LPN : 8 / VPL);
     static constexpr int IPL = MB / LPN;
     // a stage is SS items (SS*VPL 16-byte slots per lane); NBUF stage
     // buffers, NBUF-1 stages in flight while one is summed
@@ -76,7 +84,7 @@ struct KCfg {
     static constexpr int SPB = MB / SS;                        // stages per decoded batch
     // (shapes whose batch is a single stage keep two buffers of 8 items)
     static constexpr int NBUF = NBUF_ < 2 ? 2 : NBUF_;
-    static constexpr int STAGE_BYTES = NBUF * SS * VPL * 32 * 16;  // per warp
+    static constexpr int STAGE_BYTES0 = NBUF * SS * VPL * 32 * 16;  // per warp
     // the stage issued NBUF-1 stages ahead lies at most REL batches past the
     // current one; one more batch is decoded so that its column indices load
     // a batch before their gathers issue
@@ -84,11 +92,28 @@ struct KCfg {
     static constexpr int DEPTH = REL + 2;
     // stage copies: bulk copies on the TMA engine (1) or 16-byte cp.async (0)
     static constexpr bool TMA = SPMM_TMA != 0;
+    // Item ring (RING > 0): every item is its own cp.async group in a ring of
+    // RING item slots per warp, so RING-1 items are in flight while one is
+    // summed (the stage buffers above keep one whole stage out of flight).
+    // The loop is unrolled over U items (a multiple of the batch and of the
+    // ring); an item is issued RING-1 items before it is summed, which reaches
+    // RMAXB batches past the one being summed.
+    // (RING counts 16-byte slots per lane: items of VPL vectors get RING/VPL)
+    static constexpr int RING = SPMM_RING == 0 ? 0
+                                : (SPMM_RING / VPL < 2 ? 2 : SPMM_RING / VPL);
+    static constexpr int U = RING > MB ? RING : MB;
+    static constexpr int BPI = U / MB;
+    static constexpr int RMAXB = RING > 0 ? (U - 1 + RING - 1) / MB : 0;
+    static constexpr int RDEPTH = RMAXB + 1;
+    static constexpr int RING_BYTES = RING * VPL * 32 * 16;   // per warp
+    static constexpr int STAGE_BYTES = RING > 0 ? RING_BYTES : STAGE_BYTES0;
     // resident CTAs per SM the register budget targets
     static constexpr int MINB = (LPN <= 8 && VPL == 1) ? SPMM_MINBLOCKS_NARROW : SPMM_MINBLOCKS;
-    static_assert(DEPTH <= 4, "at most four decoded batches");
+    static_assert(DEPTH <= 8, "at most eight decoded batches");
     static_assert(!TMA || NBUF == 2, "bulk-copy staging uses two buffers");
     static_assert(SPB == 1 || IPL == 1, "split batches need one item per lane");
+    static_assert(RING == 0 || (U % RING == 0 && U % MB == 0 && !TMA),
+                  "the ring divides the unrolled items");
 };
 
 // Dynamic shared memory of a persistent CTA of `warps` warps: a pair of
@@ -270,6 +295,7 @@ struct ItemBatch {
     float val[K::IPL];    // its value, times b_scale[col] (0 for other items)
     uint32_t ends;        // bit t: item t ends a row
     uint32_t nz;          // bit t: item t is a nonzero
+    uint32_t any_end;     // bit t: item t ends a row in some group of the warp (warp-uniform)
 };
 
 // OR of a per-lane MB-bit mask over the lanes of each group.
@@ -282,6 +308,26 @@ __device__ __forceinline__ uint32_t group_or(uint32_t m, int g) {
     } else {
 #pragma unroll
         for (int off = 1; off < K::LPN; off <<= 1) m |= __shfl_xor_sync(kFull, m, off);
+        return m;
+    }
+}
+
+// The same, and `any` receives the OR over the whole warp (the same value in
+// every lane).
+template <class K>
+__device__ __forceinline__ uint32_t group_or(uint32_t m, int g, uint32_t& any) {
+    if constexpr (K::IPL == 1) {
+        // MB == LPN: the G group masks sit side by side in one word
+        const uint32_t all = __reduce_or_sync(kFull, m << (g * K::LPN));
+        uint32_t a = all;
+#pragma unroll
+        for (int sh = 16; sh >= K::LPN; sh >>= 1) a |= a >> sh;
+        any = a & low_bits<K::LPN>();
+        return K::LPN == 32 ? all : ((all >> (g * K::LPN)) & low_bits<K::LPN>());
+    } else {
+#pragma unroll
+        for (int off = 1; off < K::LPN; off <<= 1) m |= __shfl_xor_sync(kFull, m, off);
+        any = __reduce_or_sync(kFull, m);
         return m;
     }
 }
@@ -341,6 +387,20 @@ __device__ __forceinline__ bool walk_unit(const Problem& p, int i, int j, int cs
     const int tail_row = (rs0 < y0 && x0 < x1) ? x0 : -1;
     const bool head = (cs >= 0) && x1 < row_hi && y1 > rs1;
 
+#if SPMM_ENDS_BITMAP
+    // Row ends come from the plan's bitmap over the merge items: the chunk's
+    // items are global items x0 + y0 .. x1 + y1 - 1, and batch b's mask is
+    // the MB bits from item x0 + y0 + b*MB on, read as a 64-bit window of two
+    // words.  The words of the next batch are loaded one batch ahead.
+    const uint32_t item0 = (uint32_t)x0 + (uint32_t)y0;
+    uint32_t w_lo = 0, w_hi = 0;
+    auto load_words = [&](int b_off) {
+        const uint32_t pos = item0 + (uint32_t)b_off;
+        w_lo = __ldg(p.ends + (pos >> 5));
+        w_hi = __ldg(p.ends + (pos >> 5) + 1);
+    };
+    load_words(0);
+#else
     int pg_cur[IPL], pg_nxt[IPL], pg_nx2[IPL];
     auto load_page = [&](int q, int* out) {
 #pragma unroll
@@ -353,9 +413,20 @@ __device__ __forceinline__ bool walk_unit(const Problem& p, int i, int j, int cs
     load_page(1, pg_nxt);
     load_page(2, pg_nx2);
     int pq = 2;
+#endif
 
     int beta = 0, e = y0;   // next batch: first item, first nonzero
     auto decode = [&](ItemBatch<K>& B) {
+        const int left = nitems - beta;
+        const uint32_t valid =
+            left >= MB ? low_bits<MB>() : (left > 0 ? ((1u << left) - 1u) : 0u);
+#if SPMM_ENDS_BITMAP
+        uint32_t m = __funnelshift_r(w_lo, w_hi, (item0 + (uint32_t)beta) & 31u) & valid;
+        if (beta + MB < nitems) load_words(beta + MB);
+        // every lane of a group computes the same mask; the warp's OR marks the
+        // items where some group ends a row
+        const uint32_t any = __reduce_or_sync(kFull, m);
+#else
         uint32_t m = 0;
 #pragma unroll
         for (int u = 0; u < IPL; ++u) {
@@ -364,11 +435,12 @@ __device__ __forceinline__ bool walk_unit(const Problem& p, int i, int j, int cs
             if (d0 < (unsigned)MB) m |= 1u << d0;
             if (d1 < (unsigned)MB) m |= 1u << d1;
         }
-        m = group_or<K>(m, g);
-        const int left = nitems - beta;
-        const uint32_t valid =
-            left >= MB ? low_bits<MB>() : (left > 0 ? ((1u << left) - 1u) : 0u);
+        uint32_t any;
+        m = group_or<K>(m, g, any);
         m &= valid;
+#endif
+        // items past a group's walk are never row ends, so the warp's OR needs no mask
+        B.any_end = any;
         const uint32_t nz = valid & ~m;
 #pragma unroll
         for (int u = 0; u < IPL; ++u) {
@@ -388,6 +460,7 @@ __device__ __forceinline__ bool walk_unit(const Problem& p, int i, int j, int cs
         B.nz = nz;
         e += __popc(nz);
         beta += MB;
+#if !SPMM_ENDS_BITMAP
         // A batch closes at most MB rows, so at most one page runs out per batch.
         const int last = __shfl_sync(kFull, pg_cur[IPL - 1], LPN - 1, LPN);
         if (last < beta) {
@@ -399,6 +472,7 @@ __device__ __forceinline__ bool walk_unit(const Problem& p, int i, int j, int cs
             ++pq;
             load_page(pq, pg_nx2);
         }
+#endif
     };
 
     float2 acc[K::NE / 2];
@@ -413,7 +487,9 @@ __device__ __forceinline__ bool walk_unit(const Problem& p, int i, int j, int cs
         const float2 a2 = make_float2(a, a);
 #pragma unroll
         for (int q = 0; q < VPL; ++q) fma_vec<typename K::TB>(acc + q * (K::EPV / 2), a2, v[q]);
-        if ((X.ends >> tt) & 1u) {
+        // the warp-uniform test skips the per-group test (and its divergent
+        // branch) on the items where no group of the warp ends a row
+        if (((X.any_end >> tt) & 1u) && ((X.ends >> tt) & 1u)) {
             const int row = cur_row++;
             if (row == tail_row) store_slot<K>(p, 2 * (int64_t)gc, acc, lc);
             else store_vecs<K, VPL, LPN>(p, row, acc, lc);
@@ -429,6 +505,7 @@ __device__ __forceinline__ bool walk_unit(const Problem& p, int i, int j, int cs
 
     // cp.async staging: slot (s, q) of lane l at buf + (s*VPL + q)*512 + l*16
     // holds vector q of item s of the lane's group; padding slots are zeroed.
+    const uint64_t bpol = b_gather_policy();
     auto issue_lsu = [&](int t, const ItemBatch<K>& X, int h) {
         const uint32_t buf = wbase + lane * 16 + (uint32_t)(t % K::NBUF) * kStage;
 #pragma unroll
@@ -441,11 +518,12 @@ __device__ __forceinline__ bool walk_unit(const Problem& p, int i, int j, int cs
                 tt = h * SS + s;
                 cc = __shfl_sync(kFull, X.col[0], tt, LPN);
             }
-            const int ok = ((X.nz >> tt) & 1u) ? 16 : 0;
+            const bool skip = !((X.nz >> tt) & 1u);
             const char* rp = brow(lc, cc);
 #pragma unroll
             for (int q = 0; q < VPL; ++q)
-                cp_async16(buf + (uint32_t)((s * VPL + q) * 32 * 16), rp + lc.qoff[q], ok);
+                cp_async16_zero_if_hint(buf + (uint32_t)((s * VPL + q) * 32 * 16),
+                                        rp + lc.qoff[q], skip, bpol);
         }
         cp_async_commit();
     };
@@ -513,6 +591,56 @@ __device__ __forceinline__ bool walk_unit(const Problem& p, int i, int j, int cs
     };
 
     const int nb = (__reduce_max_sync(kFull, nitems) + MB - 1) / MB;
+    if constexpr (K::RING > 0) {
+        constexpr int RING = K::RING, U = K::U, BPI = K::BPI, RD = K::RDEPTH;
+        // slot k of lane l: wbase + k*VPL*512 + l*16 (+ q*512 for vector q)
+        const uint32_t rbase = wbase + lane * 16;
+        ItemBatch<K> qr[RD];   // qr[r]: batch b + r, b the first batch of the iteration
+#pragma unroll
+        for (int r = 0; r < RD; ++r) decode(qr[r]);
+        auto issue_item = [&](const ItemBatch<K>& X, int pos, int slot) {
+            const int cc = __shfl_sync(kFull, X.col[pos / LPN], pos % LPN, LPN);
+            const bool skip = !((X.nz >> pos) & 1u);
+            const char* rp = brow(lc, cc);
+#pragma unroll
+            for (int q = 0; q < VPL; ++q)
+                cp_async16_zero_if(rbase + (uint32_t)((slot * VPL + q) * 512), rp + lc.qoff[q],
+                                   skip);
+            cp_async_commit();
+        };
+        // prologue: items 0 .. RING-2 (items past the walk are zero-filled)
+#pragma unroll
+        for (int k = 0; k < RING - 1; ++k) issue_item(qr[k / MB], k % MB, k % RING);
+        const int iters = (nb * MB + U - 1) / U;
+#pragma unroll 1
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int s = 0; s < U; ++s) {
+                const int n = s + RING - 1;            // item issued at this step
+                issue_item(qr[n / MB], n % MB, n % RING);
+                cp_async_wait<RING - 1>();             // item s has landed
+                const ItemBatch<K>& X = qr[s / MB];
+                const int pos = s % MB;
+                const float a = __shfl_sync(kFull, X.val[pos / LPN], pos % LPN, LPN);
+                uint4 v[VPL];
+#pragma unroll
+                for (int q = 0; q < VPL; ++q)
+                    v[q] = lds128(rbase + (uint32_t)(((s % RING) * VPL + q) * 512));
+                take_item(X, pos, a, v);
+            }
+#pragma unroll
+            for (int r = 0; r < RD; ++r) {
+                if (r + BPI < RD) qr[r] = qr[r + BPI];
+                else decode(qr[r]);
+            }
+        }
+        // the zero-fills issued past the walk must land before the slots are reused
+        cp_async_wait<0>();
+        if (tail_row >= 0)
+            piece_row<K>(p, i, j, gc, tail_row, true, nullptr, lc, tq, gmask, leader);
+        if (head) piece_row<K>(p, i, j, gc, x1, false, acc, lc, tq, gmask, leader);
+        return true;
+    }
     const int nst = nb * SPB;
     // q[r]: batch b + r, b the batch being summed
     ItemBatch<K> q[K::DEPTH];

@@ -42,7 +42,9 @@ template <class TA, class TB>
 cudaError_t launch_pair(int lpn, int vpl, const Problem& p, const LaunchOpts& o, cudaStream_t s) {
     switch (lpn * 10 + vpl) {
         case 21: return launch_one<TA, TB, 2, 1>(p, o, s);
+        case 24: return launch_one<TA, TB, 2, 4>(p, o, s);
         case 41: return launch_one<TA, TB, 4, 1>(p, o, s);
+        case 42: return launch_one<TA, TB, 4, 2>(p, o, s);
         case 81: return launch_one<TA, TB, 8, 1>(p, o, s);
         case 161: return launch_one<TA, TB, 16, 1>(p, o, s);
         case 321: return launch_one<TA, TB, 32, 1>(p, o, s);
@@ -66,18 +68,38 @@ cudaError_t launch_wide_pair(int lpn, int nv, const Problem& p, const LaunchOpts
     }
 }
 
-template <class TA, class TB>
-cudaError_t launch_batched(const BatchEntry* table, const int64_t* item_base, int count, char* ws,
-                           int* counter, int64_t max_items, int ctas_per_sm, cudaStream_t s) {
+template <class TA, class TB, int LPN>
+cudaError_t launch_batched_one(const BatchEntry* table, const int64_t* item_base, int count,
+                               char* ws, int* counter, int64_t max_items, int ctas_per_sm,
+                               cudaStream_t s) {
     static std::atomic<int> cache[kMaxDevices][3];
-    auto kern = spmm_csr_batched_kernel<TA, TB>;
+    auto kern = spmm_csr_batched_kernel<TA, TB, LPN>;
     const int threads = kBatchWarps * 32;
-    const size_t smem = (size_t)smem_bytes(kBatchWarps, batch_stage_bytes<TA, TB>());
+    const size_t smem = (size_t)smem_bytes(kBatchWarps, batch_stage_bytes<TA, TB, LPN>());
     const int per_sm = cached_ctas_per_sm(kern, threads, smem, cache);
     if (per_sm == 0) return cudaErrorInvalidValue;
     const int64_t grid = persistent_grid(per_sm, ctas_per_sm, max_items, kBatchWarps);
     kern<<<(unsigned)grid, threads, smem, s>>>(table, item_base, count, ws, counter);
     return cudaGetLastError();
+}
+
+template <class TA, class TB>
+cudaError_t launch_batched(int lpn, const BatchEntry* table, const int64_t* item_base, int count,
+                           char* ws, int* counter, int64_t max_items, int ctas_per_sm,
+                           cudaStream_t s) {
+    switch (lpn) {
+        case 2: return launch_batched_one<TA, TB, 2>(table, item_base, count, ws, counter,
+                                                     max_items, ctas_per_sm, s);
+        case 4: return launch_batched_one<TA, TB, 4>(table, item_base, count, ws, counter,
+                                                     max_items, ctas_per_sm, s);
+        case 8: return launch_batched_one<TA, TB, 8>(table, item_base, count, ws, counter,
+                                                     max_items, ctas_per_sm, s);
+        case 16: return launch_batched_one<TA, TB, 16>(table, item_base, count, ws, counter,
+                                                       max_items, ctas_per_sm, s);
+        case 32: return launch_batched_one<TA, TB, 32>(table, item_base, count, ws, counter,
+                                                       max_items, ctas_per_sm, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace spmm
@@ -91,10 +113,10 @@ cudaError_t launch_batched(const BatchEntry* table, const int64_t* item_base, in
                                       const LaunchOpts& o, cudaStream_t s) {              \
         return launch_pair<TA, TB>(lpn, vpl, p, o, s);                                    \
     }                                                                                     \
-    cudaError_t launch_batched_##a##_##b(const BatchEntry* t, const int64_t* ib, int n,  \
-                                         char* ws, int* ctr, int64_t mx, int cps,         \
+    cudaError_t launch_batched_##a##_##b(int lpn, const BatchEntry* t, const int64_t* ib, \
+                                         int n, char* ws, int* ctr, int64_t mx, int cps,  \
                                          cudaStream_t s) {                                \
-        return launch_batched<TA, TB>(t, ib, n, ws, ctr, mx, cps, s);                     \
+        return launch_batched<TA, TB>(lpn, t, ib, n, ws, ctr, mx, cps, s);                \
     }                                                                                     \
     }
 
