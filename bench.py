@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--kernel", type=int, default=0,
                     help="spmm_tuning.kernel: 0 library default, 1 staged 16-byte kernel, "
                          "2 32-byte-lane kernel")
+    ap.add_argument("--ksplit", type=int, default=0,
+                    help="gather workload: also time the gathers in the orders of a K-split "
+                         "3D grid with this many k-blocks")
     ap.add_argument("--lanes", type=int, default=0,
                     help="spmm_tuning.lanes_per_item: 0 default, 2 or 4 lanes per column "
                          "block of 4 or 8 vectors")
@@ -902,6 +905,25 @@ def run_gather(args):
     streams = {"rmat": A.colind,
                "uniform": inputs_uniform_cols(nnz, K, 11, dev),
                "l2_resident": inputs_uniform_cols(nnz, min(K, 60000), 12, dev)}
+    if args.ksplit > 1:
+        # the same gathers in the orders a K-split 3D grid (Section 3.4's
+        # reservation over (i, j, k) tiles) would issue them, with K cut into
+        # `ksplit` blocks: "ksplit_tile" sweeps the k-blocks inside each C row
+        # block (stationary C, a row block's C slice kept in L2), and
+        # "ksplit_kmajor" sweeps every row block inside each k-block (B's
+        # k-block slice kept in L2).  The gathered bytes are the same.
+        TRg = 16
+        RB = -(-M // TRg)
+        KB = -(-K // args.ksplit)
+        row_of = torch.repeat_interleave(torch.arange(M, device=dev),
+                                         (A.rowptr[1:] - A.rowptr[:-1]).long())
+        rb = row_of // RB
+        kb = A.colind.long() // KB
+        pos = torch.arange(nnz, device=dev)
+        for name, key in (("ksplit_tile", (rb * args.ksplit + kb) * nnz + pos),
+                          ("ksplit_kmajor", (kb * TRg + rb) * nnz + pos)):
+            streams[name] = A.colind[torch.argsort(key)].contiguous()
+        del row_of, rb, kb, pos
     gathered = nnz * N * 4
 
     def timed(fn, reps=5):

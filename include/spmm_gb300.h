@@ -278,8 +278,9 @@ int spmm_batch_graph_launch(spmm_batch batch, void* workspace, size_t workspace_
 
 /* Choose row blocks {1,4}, column blocks {1,2} and chunk size {256..2048} per
  * size class (same N, rows below 10k / 50k / above) by coordinate descent,
+ * then the resident CTAs per SM of the launches (as many as fit, 2 or 1),
  * timing `reps` batched launches per candidate with CUDA events; leaves the
- * batch planned with the best shapes and returns the best time in *best_ms. */
+ * batch planned with the best choices and returns the best time in *best_ms. */
 int spmm_batch_autotune(spmm_batch batch, void* workspace, size_t workspace_bytes, int32_t reps,
                         void* stream, float* best_ms);
 

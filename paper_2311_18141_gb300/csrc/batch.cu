@@ -439,6 +439,27 @@ extern "C" int spmm_batch_autotune(spmm_batch b, void* workspace, size_t workspa
         st = batch_build(b, s);
         if (st) return st;
     }
+    // then the resident CTAs per SM of the launches (fewer CTAs leave each
+    // warp more of the L2 and the memory pipes)
+    const int32_t cps_c[] = {2, 1};
+    int32_t best_cps = b->ctas_per_sm;
+    for (int32_t cps : cps_c) {
+        if (cps == best_cps) continue;
+        b->ctas_per_sm = cps;
+        float ms = 0.0f;
+        st = time_batch(b, workspace, workspace_bytes, reps, s, &ms);
+        if (st) return st;
+        if (ms < best) {
+            best = ms;
+            best_cps = cps;
+        }
+    }
+    b->ctas_per_sm = best_cps;
+    if (b->graph) {   // the captured launch carries the grid size
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+        b->graph_ws = nullptr;
+    }
     if (best_ms) *best_ms = best;
     return SPMM_OK;
 }

@@ -66,34 +66,6 @@ __device__ __forceinline__ void cp_async16_zero_if(uint32_t smem_addr, const voi
 #endif
                  :: "r"(smem_addr), "l"(gptr), "r"((int)skip) : "memory");
 }
-// L2 eviction priority for B gathers (SPMM_B_L2_HINT): 0 none; 1 evict_last
-// (B rows outrank the streaming A and C lines); 2 evict_first.  The policy
-// word is created by createpolicy in the thread that uses it (a cache-policy
-// operand must come from createpolicy; its encoding is opaque) and passed as
-// the last operand of cp.async, after the ignore-src predicate.
-#ifndef SPMM_B_L2_HINT
-#define SPMM_B_L2_HINT 0
-#endif
-__device__ __forceinline__ uint64_t b_gather_policy() {
-    uint64_t pol = 0;
-#if SPMM_B_L2_HINT == 1
-    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0;" : "=l"(pol));
-#elif SPMM_B_L2_HINT == 2
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0;" : "=l"(pol));
-#endif
-    return pol;
-}
-__device__ __forceinline__ void cp_async16_zero_if_hint(uint32_t smem_addr, const void* gptr,
-                                                        bool skip, uint64_t pol) {
-#if SPMM_B_L2_HINT
-    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t"
-                 "cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, q, %3;\n\t}"
-                 :: "r"(smem_addr), "l"(gptr), "r"((int)skip), "l"(pol) : "memory");
-#else
-    (void)pol;
-    cp_async16_zero_if(smem_addr, gptr, skip);
-#endif
-}
 __device__ __forceinline__ void cp_async_commit() {
     asm volatile("cp.async.commit_group;" ::: "memory");
 }

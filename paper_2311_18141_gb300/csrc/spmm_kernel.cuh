@@ -505,7 +505,6 @@ __device__ __forceinline__ bool walk_unit(const Problem& p, int i, int j, int cs
 
     // cp.async staging: slot (s, q) of lane l at buf + (s*VPL + q)*512 + l*16
     // holds vector q of item s of the lane's group; padding slots are zeroed.
-    const uint64_t bpol = b_gather_policy();
     auto issue_lsu = [&](int t, const ItemBatch<K>& X, int h) {
         const uint32_t buf = wbase + lane * 16 + (uint32_t)(t % K::NBUF) * kStage;
 #pragma unroll
@@ -522,8 +521,8 @@ __device__ __forceinline__ bool walk_unit(const Problem& p, int i, int j, int cs
             const char* rp = brow(lc, cc);
 #pragma unroll
             for (int q = 0; q < VPL; ++q)
-                cp_async16_zero_if_hint(buf + (uint32_t)((s * VPL + q) * 32 * 16),
-                                        rp + lc.qoff[q], skip, bpol);
+                cp_async16_zero_if(buf + (uint32_t)((s * VPL + q) * 32 * 16), rp + lc.qoff[q],
+                                   skip);
         }
         cp_async_commit();
     };
