@@ -74,7 +74,8 @@ def parse():
     ap.add_argument("--spgemm-scale", type=int, default=14,
                     help="R-MAT scale of the A*A SpGEMM workload")
     ap.add_argument("--workload", default="rmat",
-                    choices=["rmat", "precision", "gcn", "batch", "spgemm", "loadsim", "gather"],
+                    choices=["rmat", "precision", "gcn", "batch", "spgemm", "loadsim", "gather",
+                             "ksplit"],
                     help="rmat: the benchmark line; the others report the precision, "
                          "backward and batched forms")
     return ap.parse_args()
@@ -965,6 +966,61 @@ def run_gather(args):
                       "gathered_bytes": gathered, "results": res}), flush=True)
 
 
+def run_ksplit(args):
+    """The K-split 3D grid of Section 3.4's reservation over (i, j, k) tiles,
+    measured from its work.  A's rows are cut by k-block into sub-rows (the
+    (row, k-block) pairs that hold nonzeros), ordered by C row block, then
+    k-block, then row: a row block's k-blocks one after the other, so its C
+    slice stays in L2 while B's k-blocks go by.  spmm_csr multiplies that
+    matrix by B at the benchmark's 16 x 4 grid, so every gather a K-split
+    kernel would issue is issued in its order and every partial row is
+    written once.  A K-split kernel must in addition add the partial rows of
+    a row into C, so this time is a lower bound on its time."""
+    import torch
+    from paper_2311_18141_gb300 import binding
+    dev = torch.device("cuda")
+    binding.load_library()
+    A, B = make_workload(args.scale, args.n, dev)
+    M, K, N, nnz = A.M, A.K, args.n, A.nnz
+    TR, TC = (int(x) for x in args.grid.split("x"))
+    stream = torch.cuda.current_stream()
+    tun = binding.make_tuning(tile_order=args.order)
+
+    def product_ms(rowptr, colind, vals, rows):
+        C = torch.empty(rows, N, device=dev)
+        plan = binding.Plan(rowptr, rows, K, nnz, N, TR, TC, tuning=tun)
+        ws = binding.workspace(plan.workspace_bytes, dev)
+        ms = _time_ms(lambda: binding.spmm_csr(rowptr, colind, vals, B, C, rows, K, N, nnz,
+                                               plan=plan, ws=ws, stream=stream),
+                      args.steps, args.warmup, stream)
+        assert binding.spmm_get_device_status(ws) == 0
+        plan.close()
+        return ms
+
+    out = {"plain_ms": product_ms(A.rowptr, A.colind, A.vals, M)}
+    RB = -(-M // TR)
+    row_of = torch.repeat_interleave(torch.arange(M, device=dev),
+                                     (A.rowptr[1:] - A.rowptr[:-1]).long())
+    for nk in (2, 4, 16):
+        KB = -(-K // nk)
+        key = ((row_of // RB) * nk + A.colind.long() // KB) * M + row_of
+        key, perm = torch.sort(key, stable=True)
+        _, counts = torch.unique_consecutive(key, return_counts=True)
+        rows = int(counts.numel())
+        rowptr = torch.zeros(rows + 1, dtype=torch.int32, device=dev)
+        rowptr[1:] = torch.cumsum(counts, 0).to(torch.int32)
+        colind = A.colind[perm].contiguous()
+        vals = A.vals[perm].contiguous()
+        del key, perm, counts
+        ms = product_ms(rowptr, colind, vals, rows)
+        out[f"k{nk}"] = {"sub_rows": rows, "ms_lower_bound": ms,
+                         "partial_rows_per_row": rows / M}
+        del rowptr, colind, vals
+        torch.cuda.empty_cache()
+    print(json.dumps({"workload": f"ksplit-rmat-s{args.scale}-n{N}-grid{args.grid}", "nnz": nnz,
+                      "results": out}), flush=True)
+
+
 def inputs_uniform_cols(nnz, K, seed, device):
     """nnz column indices uniform in [0, K), from the counter-based generator."""
     import torch
@@ -1010,6 +1066,9 @@ def main():
         return
     if args.workload == "gather":
         run_gather(args)
+        return
+    if args.workload == "ksplit":
+        run_ksplit(args)
         return
     if args.workload == "precision":
         run_precision(args)

@@ -206,7 +206,7 @@ int spmm_plan_create(spmm_plan* plan, const int32_t* A_rowptr, int64_t M, int64_
     resolve_tuning(tuning, &p->tuning);
     p->D = p->tuning.chunk_items > 0 ? p->tuning.chunk_items
                                     : plan_default_chunk(M, nnz, tile_cols, device_sm_count(),
-                                                         plan_default_groups_wide(N, tile_cols));
+                                                         plan_default_groups(N, tile_cols));
     p->tuning.chunk_items = p->D;
     p->cap = plan_chunk_cap(M, nnz, tile_rows, p->D);
     const size_t arrays = plan_array_bytes(tile_rows, p->cap);
@@ -278,7 +278,7 @@ int spmm_csr_workspace_size(int64_t M, int64_t nnz, int64_t N, int32_t tile_rows
     if (st) return st;
     (void)tuning;  // a call without a plan always uses the default tuning
     const int32_t D = plan_default_chunk(M, nnz, tile_cols, device_sm_count(),
-                                         plan_default_groups_wide(N, tile_cols));
+                                         plan_default_groups(N, tile_cols));
     const int64_t cap = plan_chunk_cap(M, nnz, tile_rows, D);
     *bytes = plan_array_bytes(tile_rows, cap) + plan_ends_bytes(M + nnz) +
              scratch_layout(tile_rows, tile_cols, cap, N).total;
@@ -342,7 +342,7 @@ int spmm_csr(const int32_t* A_rowptr, const int32_t* A_colind, const void* A_val
     } else {
         resolve_tuning(nullptr, &tun);
         RB = (int32_t)((M + TR - 1) / TR);
-        D = plan_default_chunk(M, nnz, TC, device_sm_count(), plan_default_groups_wide(N, TC));
+        D = plan_default_chunk(M, nnz, TC, device_sm_count(), plan_default_groups(N, TC));
         cap = plan_chunk_cap(M, nnz, TR, D);
         // layout [scratch: status, counters, slots][plan arrays]: the status
         // word stays at the start of the caller's workspace

@@ -132,7 +132,7 @@ int32_t plan_default_chunk(int64_t M, int64_t nnz, int32_t TC, int sms, int grou
     if (groups < 1) groups = 1;
     // about 16 units per warp of the full grid, a unit being `groups` chunks
     int64_t d = ceil_div((M + nnz) * (int64_t)TC, 16 * nwarps * groups);
-    if (d < 128) d = 128;
+    if (d < 32) d = 32;   // small problems: enough units to spread over the SMs
     if (d > 16384) d = 16384;
     d = ceil_div(d, 32) * 32;
     return (int32_t)d;
@@ -142,17 +142,6 @@ int plan_default_groups(int64_t N, int32_t TC) {
     if (TC < 1) TC = 1;
     const int64_t nvec = ((N + TC - 1) / TC + 3) / 4;   // FP32 vectors of a column block
     if (nvec >= 32) return 1;
-    int lpn = 2;
-    while (lpn < nvec) lpn <<= 1;
-    return 32 / lpn;
-}
-
-int plan_default_groups_wide(int64_t N, int32_t TC) {
-    if (TC < 1) TC = 1;
-    const int64_t w = ((N + TC - 1) / TC + 3) / 4 * 4;   // FP32 columns of a block
-    if ((w * 4) % 32 != 0 || (N * 4) % 32 != 0) return plan_default_groups(N, TC);
-    const int64_t nvec = w * 4 / 32;                     // 32-byte vectors of a block
-    if (nvec < 2 || nvec > 32) return plan_default_groups(N, TC);
     int lpn = 2;
     while (lpn < nvec) lpn <<= 1;
     return 32 / lpn;

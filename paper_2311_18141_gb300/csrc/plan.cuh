@@ -10,12 +10,9 @@ namespace spmm {
 int64_t plan_chunk_cap(int64_t M, int64_t nnz, int32_t TR, int32_t D);
 // Default merge-path items per chunk: about 16 units per resident warp.
 int32_t plan_default_chunk(int64_t M, int64_t nnz, int32_t TC, int sms, int groups);
-// Lane groups per warp of the 16-byte staged FP32 kernel shape for N columns
-// in TC blocks.
+// Lane groups per warp of the staged kernel's FP32 shape for N columns in TC
+// blocks (the default kernel).
 int plan_default_groups(int64_t N, int32_t TC);
-// The same for the kernel an FP32 product runs by default: the 32-byte-lane
-// kernel when a column block is whole 32-byte vectors, else the staged one.
-int plan_default_groups_wide(int64_t N, int32_t TC);
 // Bytes of the plan arrays (blk_base, bnd_row, bnd_nnz), 256-byte padded.
 size_t plan_array_bytes(int32_t TR, int64_t cap);
 // Split a plan-array region into its three arrays.
