@@ -392,6 +392,8 @@ int spmm_csr(const int32_t* A_rowptr, const int32_t* A_colind, const void* A_val
         const LaunchFn fn = spmm_launcher(a_dtype, b_dtype);
         if (!fn) return SPMM_ERR_UNSUPPORTED;
         e = fn(lpn, vpl, p, o, s);
+        // the staged kernel leaves split rows in the slots
+        if (e == cudaSuccess) e = launch_split_row_fixup(p, cap + TR, s);
     }
     return e == cudaSuccess ? SPMM_OK : SPMM_ERR_CUDA;
 }

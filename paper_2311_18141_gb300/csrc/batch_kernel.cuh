@@ -49,8 +49,8 @@ __host__ __device__ constexpr int batch_stage_bytes() {
 // Unit u of a problem in column block j: its sub-chunks u*G .. u*G+G-1, counted
 // over all row blocks, one per lane group; each group finds its own row block.
 template <class TA, class TB, int LPN>
-__device__ __forceinline__ bool batch_unit(const Problem& p, int u, int j, int lane,
-                                           uint32_t wbase, uint32_t bar0, uint32_t& phases) {
+__device__ __forceinline__ void batch_unit(const Problem& p, int u, int j, int lane,
+                                           uint32_t wbase) {
     using K = KCfg<TA, TB, LPN, 1, SPMM_BATCH_NBUF>;
     const LaneCols<K::VPL> lc = lane_cols<K, K::VPL, K::LPN>(p, j, lane % K::LPN);
     const int gsc = u * K::G + lane / K::LPN;
@@ -64,7 +64,7 @@ __device__ __forceinline__ bool batch_unit(const Problem& p, int u, int j, int l
         }
         cs = gsc - p.blk_base[il];
     }
-    return walk_unit<K>(p, il, j, cs, lc, lane, wbase, bar0, phases);
+    walk_unit<K, false>(p, il, j, cs, lc, lane, wbase);
 }
 
 // The products of one lane shape (LPN lanes per column block) of a batch:
@@ -80,8 +80,7 @@ spmm_csr_batched_kernel(const BatchEntry* __restrict__ table,
     __shared__ Problem sp[kBatchWarps];
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
-    uint32_t bar0 = 0, phases = 0;
-    const uint32_t wbase = warp_staging<K>(lane, bar0);
+    const uint32_t wbase = warp_staging<K>();
     const int64_t first = item_base[0];
     const int64_t total = item_base[count] - first;
     int cur = -1;   // product whose descriptor is in sp[w]
@@ -117,7 +116,7 @@ spmm_csr_batched_kernel(const BatchEntry* __restrict__ table,
         const int local = (int)(abs_item - item_base[lo]);
         const int u = local / p.TC;
         const int j = local - u * p.TC;
-        if (!batch_unit<TA, TB, LPN>(p, u, j, lane, wbase, bar0, phases)) return;
+        batch_unit<TA, TB, LPN>(p, u, j, lane, wbase);
     }
 }
 

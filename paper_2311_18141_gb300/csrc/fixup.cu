@@ -1,0 +1,92 @@
+// Split rows of the staged product, summed after the persistent launch.
+//
+// The plan cuts a row block's merge path into chunks; a chunk boundary inside
+// a (heavy) row splits it.  While walking, the chunk where such a row begins
+// and every chunk fully inside it leave a head piece in workspace slot
+// 2*gc + 1, and the chunk where it ends leaves a tail piece in slot 2*gc (gc
+// the global chunk).  Once the launch is over, this kernel sums each split
+// row's pieces in chunk order and writes C = beta*C + a_scale*sum: the same
+// sums, in the same order, that the last-arriving piece would form inside the
+// walk, without the acquire-release atomics that ordering needs there.
+#include "api_internal.cuh"
+#include "launch.cuh"
+
+namespace spmm {
+
+namespace {
+
+// One warp per plan boundary (the boundaries of row block i sit at
+// blk_base[i] + i + c, c = 0 .. chunks of the block).  The warp of the first
+// boundary strictly inside row r -- the one that ends the chunk where r
+// begins -- does r; every other warp returns at once.
+__global__ void __launch_bounds__(256) split_row_fixup_kernel(const Problem p) {
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t total = (int64_t)p.blk_base[p.TR] + p.TR;
+    if (warp >= total) return;
+    const int b = (int)warp;
+    int lo = 0, hi = p.TR - 1;   // largest i with blk_base[i] + i <= b
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.blk_base[mid] + mid <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const int i = lo;
+    const int c = b - p.blk_base[i] - i;
+    if (c < 1 || c >= p.blk_base[i + 1] - p.blk_base[i]) return;   // interior boundaries only
+    const int r = p.bnd_row[b];
+    const int row_lo = i * p.RB;
+    const int row_hi = min(p.M, row_lo + p.RB);
+    if (r < row_lo || r >= row_hi) return;
+    const int rs = __ldg(p.rowptr + r);
+    if (p.bnd_nnz[b] <= rs) return;                 // the boundary is at a row start
+    const int re = __ldg(p.rowptr + r + 1);
+    const int nnz_lo = __ldg(p.rowptr + row_lo);
+    // chunks holding r's first item and its end (chunk c spans merge-path
+    // items [c*D, (c+1)*D) of the block; boundaries inside a split row are
+    // never moved, so these are exact)
+    const int ca = (int)(((int64_t)(r - row_lo) + (rs - nnz_lo)) / p.D);
+    if (c != ca + 1) return;
+    const int cb = (int)(((int64_t)(r - row_lo) + (re - nnz_lo)) / p.D);
+    const int base = p.blk_base[i];
+    const bool scaled = p.a_scale != nullptr;
+    const float sa = scaled ? __ldg(p.a_scale + r) : 1.0f;
+    float* crow = p.C + (int64_t)r * p.ldc;
+    for (int v = lane; v < p.N / 4; v += 32) {
+        float4 s = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        for (int cc = ca; cc <= cb; ++cc) {
+            const int64_t slot = 2 * (int64_t)(base + cc) + (cc == cb ? 0 : 1);
+            const float4 t = ld_cg_f4(p.slots + slot * p.N + 4 * v);
+            s.x += t.x;
+            s.y += t.y;
+            s.z += t.z;
+            s.w += t.w;
+        }
+        if (scaled) {
+            s.x *= sa;
+            s.y *= sa;
+            s.z *= sa;
+            s.w *= sa;
+        }
+        float* d = crow + 4 * v;
+        if (p.beta != 0.0f) {
+            const float4 old = __ldcg(reinterpret_cast<const float4*>(d));
+            s.x = fmaf(p.beta, old.x, s.x);
+            s.y = fmaf(p.beta, old.y, s.y);
+            s.z = fmaf(p.beta, old.z, s.z);
+            s.w = fmaf(p.beta, old.w, s.w);
+        }
+        st_cs_f4(d, s);
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_split_row_fixup(const Problem& p, int64_t max_boundaries, cudaStream_t s) {
+    if (max_boundaries <= 0) return cudaSuccess;
+    const int64_t blocks = (max_boundaries + 7) / 8;   // 8 warps per 256-thread block
+    split_row_fixup_kernel<<<(unsigned)blocks, 256, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+}  // namespace spmm

@@ -47,16 +47,6 @@
 #ifndef SPMM_STAGE_ITEMS
 #define SPMM_STAGE_ITEMS 8 // items per lane group in one stage (of one 16-byte vector each)
 #endif
-#ifndef SPMM_RING
-#define SPMM_RING 0        // item slots of the per-item cp.async ring (0: stage buffers)
-#endif
-#ifndef SPMM_ENDS_BITMAP
-#define SPMM_ENDS_BITMAP 1 // 1: row ends from the plan's bitmap; 0: from row pointers
-#endif
-#ifndef SPMM_TMA
-#define SPMM_TMA 0         // 1: stage B rows with bulk copies on the TMA engine instead of
-                           // per-lane cp.async (correct, but slower for 128-512 byte rows)
-#endif
 
 namespace spmm {
 
@@ -84,36 +74,16 @@ struct KCfg {
     static constexpr int SPB = MB / SS;                        // stages per decoded batch
     // (shapes whose batch is a single stage keep two buffers of 8 items)
     static constexpr int NBUF = NBUF_ < 2 ? 2 : NBUF_;
-    static constexpr int STAGE_BYTES0 = NBUF * SS * VPL * 32 * 16;  // per warp
+    static constexpr int STAGE_BYTES = NBUF * SS * VPL * 32 * 16;  // per warp
     // the stage issued NBUF-1 stages ahead lies at most REL batches past the
     // current one; one more batch is decoded so that its column indices load
     // a batch before their gathers issue
     static constexpr int REL = (SPB - 1 + NBUF - 1) / SPB;
     static constexpr int DEPTH = REL + 2;
-    // stage copies: bulk copies on the TMA engine (1) or 16-byte cp.async (0)
-    static constexpr bool TMA = SPMM_TMA != 0;
-    // Item ring (RING > 0): every item is its own cp.async group in a ring of
-    // RING item slots per warp, so RING-1 items are in flight while one is
-    // summed (the stage buffers above keep one whole stage out of flight).
-    // The loop is unrolled over U items (a multiple of the batch and of the
-    // ring); an item is issued RING-1 items before it is summed, which reaches
-    // RMAXB batches past the one being summed.
-    // (RING counts 16-byte slots per lane: items of VPL vectors get RING/VPL)
-    static constexpr int RING = SPMM_RING == 0 ? 0
-                                : (SPMM_RING / VPL < 2 ? 2 : SPMM_RING / VPL);
-    static constexpr int U = RING > MB ? RING : MB;
-    static constexpr int BPI = U / MB;
-    static constexpr int RMAXB = RING > 0 ? (U - 1 + RING - 1) / MB : 0;
-    static constexpr int RDEPTH = RMAXB + 1;
-    static constexpr int RING_BYTES = RING * VPL * 32 * 16;   // per warp
-    static constexpr int STAGE_BYTES = RING > 0 ? RING_BYTES : STAGE_BYTES0;
     // resident CTAs per SM the register budget targets
     static constexpr int MINB = (LPN <= 8 && VPL == 1) ? SPMM_MINBLOCKS_NARROW : SPMM_MINBLOCKS;
     static_assert(DEPTH <= 8, "at most eight decoded batches");
-    static_assert(!TMA || NBUF == 2, "bulk-copy staging uses two buffers");
     static_assert(SPB == 1 || IPL == 1, "split batches need one item per lane");
-    static_assert(RING == 0 || (U % RING == 0 && U % MB == 0 && !TMA),
-                  "the ring divides the unrolled items");
 };
 
 // Dynamic shared memory of a persistent CTA of `warps` warps: a pair of
@@ -312,48 +282,26 @@ __device__ __forceinline__ uint32_t group_or(uint32_t m, int g) {
     }
 }
 
-// The same, and `any` receives the OR over the whole warp (the same value in
-// every lane).
-template <class K>
-__device__ __forceinline__ uint32_t group_or(uint32_t m, int g, uint32_t& any) {
-    if constexpr (K::IPL == 1) {
-        // MB == LPN: the G group masks sit side by side in one word
-        const uint32_t all = __reduce_or_sync(kFull, m << (g * K::LPN));
-        uint32_t a = all;
-#pragma unroll
-        for (int sh = 16; sh >= K::LPN; sh >>= 1) a |= a >> sh;
-        any = a & low_bits<K::LPN>();
-        return K::LPN == 32 ? all : ((all >> (g * K::LPN)) & low_bits<K::LPN>());
-    } else {
-#pragma unroll
-        for (int off = 1; off < K::LPN; off <<= 1) m |= __shfl_xor_sync(kFull, m, off);
-        any = __reduce_or_sync(kFull, m);
-        return m;
-    }
-}
-
 // One group's walk over global sub-chunk blk_base[i] + cs of row block i, in
 // column block j (cs < 0: no sub-chunk; the group still takes part in the
 // warp's shuffles).  Called by the whole warp.
 //
 // Items of the sub-chunk from merge-path point (x0, y0) to (x1, y1): the
-// nonzeros y0 .. y1-1 and the ends of rows x0 .. x1-1, in merge order, so the
-// end of row r sits at item position (rowptr[r+1] - y0) + (r - x0).  These
-// positions are read MB rows at a time ("pages", three in flight) and turned
-// into a row-end bit mask per batch of MB items; a nonzero item's index is
-// then its position minus the row ends before it.  Batches are decoded two
-// ahead of use, so their column indices are in registers when their gathers
-// are issued, and the gathers of stage t+1 are in flight while stage t is
-// summed.
+// nonzeros y0 .. y1-1 and the ends of rows x0 .. x1-1, in merge order.  Row
+// ends come from the plan's bitmap over the merge items (see decode), a
+// nonzero item's index is its position minus the row ends before it, and
+// batches are decoded two ahead of use, so their column indices are in
+// registers when their gathers are issued; the gathers of stage t+1 are in
+// flight while stage t is summed.
 //
-// `wbase` is the warp's staging region (two stage buffers); with bulk-copy
-// staging `bar0` is the warp's pair of mbarriers and `phases` their parity
-// bits, carried from unit to unit.  Returns false when a bounded wait ran out
-// (the status word then holds SPMM_ERR_TIMEOUT and the warp must stop).
-template <class K>
-__device__ __forceinline__ bool walk_unit(const Problem& p, int i, int j, int cs,
-                                          const LaneCols<K::VPL>& lc, int lane,
-                                          uint32_t wbase, uint32_t bar0, uint32_t& phases) {
+// A row that begins in an earlier sub-chunk ends here as a tail piece, and a
+// row that goes on in a later one leaves a head piece: both go to workspace
+// slots.  DEFER: the slots are summed into C afterwards by split_row_fixup
+// (no atomics in the walk); otherwise the last piece to arrive sums them
+// (piece_row).  `wbase` is the warp's staging region.
+template <class K, bool DEFER>
+__device__ __forceinline__ void walk_unit(const Problem& p, int i, int j, int cs,
+                                          const LaneCols<K::VPL>& lc, int lane, uint32_t wbase) {
     constexpr int LPN = K::LPN, MB = K::MB, IPL = K::IPL, SS = K::SS, SPB = K::SPB;
     constexpr int VPL = K::VPL;
     constexpr uint32_t kStage = SS * VPL * 32 * 16;   // bytes of one stage buffer
@@ -387,7 +335,6 @@ __device__ __forceinline__ bool walk_unit(const Problem& p, int i, int j, int cs
     const int tail_row = (rs0 < y0 && x0 < x1) ? x0 : -1;
     const bool head = (cs >= 0) && x1 < row_hi && y1 > rs1;
 
-#if SPMM_ENDS_BITMAP
     // Row ends come from the plan's bitmap over the merge items: the chunk's
     // items are global items x0 + y0 .. x1 + y1 - 1, and batch b's mask is
     // the MB bits from item x0 + y0 + b*MB on, read as a 64-bit window of two
@@ -400,45 +347,17 @@ __device__ __forceinline__ bool walk_unit(const Problem& p, int i, int j, int cs
         w_hi = __ldg(p.ends + (pos >> 5) + 1);
     };
     load_words(0);
-#else
-    int pg_cur[IPL], pg_nxt[IPL], pg_nx2[IPL];
-    auto load_page = [&](int q, int* out) {
-#pragma unroll
-        for (int u = 0; u < IPL; ++u) {
-            const int o = q * MB + tq + u * LPN;   // row offset from x0
-            out[u] = (o < x1 - x0) ? (__ldg(p.rowptr + x0 + o + 1) - y0 + o) : INT_MAX;
-        }
-    };
-    load_page(0, pg_cur);
-    load_page(1, pg_nxt);
-    load_page(2, pg_nx2);
-    int pq = 2;
-#endif
 
     int beta = 0, e = y0;   // next batch: first item, first nonzero
     auto decode = [&](ItemBatch<K>& B) {
         const int left = nitems - beta;
         const uint32_t valid =
             left >= MB ? low_bits<MB>() : (left > 0 ? ((1u << left) - 1u) : 0u);
-#if SPMM_ENDS_BITMAP
         uint32_t m = __funnelshift_r(w_lo, w_hi, (item0 + (uint32_t)beta) & 31u) & valid;
         if (beta + MB < nitems) load_words(beta + MB);
         // every lane of a group computes the same mask; the warp's OR marks the
         // items where some group ends a row
         const uint32_t any = __reduce_or_sync(kFull, m);
-#else
-        uint32_t m = 0;
-#pragma unroll
-        for (int u = 0; u < IPL; ++u) {
-            const unsigned d0 = (unsigned)(pg_cur[u] - beta);
-            const unsigned d1 = (unsigned)(pg_nxt[u] - beta);
-            if (d0 < (unsigned)MB) m |= 1u << d0;
-            if (d1 < (unsigned)MB) m |= 1u << d1;
-        }
-        uint32_t any;
-        m = group_or<K>(m, g, any);
-        m &= valid;
-#endif
         // items past a group's walk are never row ends, so the warp's OR needs no mask
         B.any_end = any;
         const uint32_t nz = valid & ~m;
@@ -460,19 +379,6 @@ __device__ __forceinline__ bool walk_unit(const Problem& p, int i, int j, int cs
         B.nz = nz;
         e += __popc(nz);
         beta += MB;
-#if !SPMM_ENDS_BITMAP
-        // A batch closes at most MB rows, so at most one page runs out per batch.
-        const int last = __shfl_sync(kFull, pg_cur[IPL - 1], LPN - 1, LPN);
-        if (last < beta) {
-#pragma unroll
-            for (int u = 0; u < IPL; ++u) {
-                pg_cur[u] = pg_nxt[u];
-                pg_nxt[u] = pg_nx2[u];
-            }
-            ++pq;
-            load_page(pq, pg_nx2);
-        }
-#endif
     };
 
     float2 acc[K::NE / 2];
@@ -539,114 +445,13 @@ __device__ __forceinline__ bool walk_unit(const Problem& p, int i, int j, int cs
         }
     };
 
-    // Bulk-copy staging: the lane that decoded a nonzero item copies the
-    // item's whole column-block segment of its B row (cbytes) with one bulk
-    // copy to buf + (g*SS + s)*RBYTES; the stage's mbarrier counts the bytes.
-    constexpr uint32_t RBYTES = LPN * VPL * 16;
-    const char* bblk = reinterpret_cast<const char*>(p.B) + (int64_t)j * p.W * K::ESZ;
-    const uint32_t cbytes =
-        (uint32_t)(((int64_t)min(p.W, p.N - j * p.W) * K::ESZ + 15) & ~(int64_t)15);
-    auto issue_tma = [&](int t, const ItemBatch<K>& X, int h) {
-        const uint32_t b = (uint32_t)(t & 1);
-        const uint32_t buf = wbase + b * kStage + (uint32_t)(g * SS) * RBYTES;
-        const uint32_t bar = bar0 + 8u * b;
-        int mine = 0;
-#pragma unroll
-        for (int u = 0; u < IPL; ++u) {
-            const int s = tq + u * LPN - h * SS;
-            if ((SPB == 1 || (unsigned)s < (unsigned)SS) && ((X.nz >> (tq + u * LPN)) & 1u)) ++mine;
-        }
-        const int total = __reduce_add_sync(kFull, mine);
-        // the buffer's previous contents were read by this warp's shared loads
-        fence_proxy_async_smem();
-        if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)total * cbytes);
-        __syncwarp();
-#pragma unroll
-        for (int u = 0; u < IPL; ++u) {
-            const int s = tq + u * LPN - h * SS;
-            if ((SPB == 1 || (unsigned)s < (unsigned)SS) && ((X.nz >> (tq + u * LPN)) & 1u))
-                bulk_g2s(buf + (uint32_t)s * RBYTES,
-                         bblk + (uint64_t)(uint32_t)X.col[u] * lc.ldb_bytes, cbytes, bar);
-        }
-    };
-    auto consume_tma = [&](int t, const ItemBatch<K>& X, int h) -> bool {
-        const uint32_t b = (uint32_t)(t & 1);
-        const bool ok = __all_sync(kFull, mbar_wait_bounded(bar0 + 8u * b, (phases >> b) & 1u));
-        phases ^= 1u << b;
-        if (!ok) return false;
-        const uint32_t buf = wbase + b * kStage + (uint32_t)(g * SS) * RBYTES + tq * 16;
-#pragma unroll
-        for (int s = 0; s < SS; ++s) {
-            const int tt = SPB == 1 ? s : h * SS + s;
-            const float a = item_val(X, s, h);
-            const bool live = (X.nz >> tt) & 1u;
-            uint4 v[VPL];
-#pragma unroll
-            for (int q = 0; q < VPL; ++q)
-                v[q] = lds128_if(buf + (uint32_t)s * RBYTES + (uint32_t)(q * LPN * 16), live);
-            take_item(X, tt, a, v);
-        }
-        return true;
-    };
-
     const int nb = (__reduce_max_sync(kFull, nitems) + MB - 1) / MB;
-    if constexpr (K::RING > 0) {
-        constexpr int RING = K::RING, U = K::U, BPI = K::BPI, RD = K::RDEPTH;
-        // slot k of lane l: wbase + k*VPL*512 + l*16 (+ q*512 for vector q)
-        const uint32_t rbase = wbase + lane * 16;
-        ItemBatch<K> qr[RD];   // qr[r]: batch b + r, b the first batch of the iteration
-#pragma unroll
-        for (int r = 0; r < RD; ++r) decode(qr[r]);
-        auto issue_item = [&](const ItemBatch<K>& X, int pos, int slot) {
-            const int cc = __shfl_sync(kFull, X.col[pos / LPN], pos % LPN, LPN);
-            const bool skip = !((X.nz >> pos) & 1u);
-            const char* rp = brow(lc, cc);
-#pragma unroll
-            for (int q = 0; q < VPL; ++q)
-                cp_async16_zero_if(rbase + (uint32_t)((slot * VPL + q) * 512), rp + lc.qoff[q],
-                                   skip);
-            cp_async_commit();
-        };
-        // prologue: items 0 .. RING-2 (items past the walk are zero-filled)
-#pragma unroll
-        for (int k = 0; k < RING - 1; ++k) issue_item(qr[k / MB], k % MB, k % RING);
-        const int iters = (nb * MB + U - 1) / U;
-#pragma unroll 1
-        for (int it = 0; it < iters; ++it) {
-#pragma unroll
-            for (int s = 0; s < U; ++s) {
-                const int n = s + RING - 1;            // item issued at this step
-                issue_item(qr[n / MB], n % MB, n % RING);
-                cp_async_wait<RING - 1>();             // item s has landed
-                const ItemBatch<K>& X = qr[s / MB];
-                const int pos = s % MB;
-                const float a = __shfl_sync(kFull, X.val[pos / LPN], pos % LPN, LPN);
-                uint4 v[VPL];
-#pragma unroll
-                for (int q = 0; q < VPL; ++q)
-                    v[q] = lds128(rbase + (uint32_t)(((s % RING) * VPL + q) * 512));
-                take_item(X, pos, a, v);
-            }
-#pragma unroll
-            for (int r = 0; r < RD; ++r) {
-                if (r + BPI < RD) qr[r] = qr[r + BPI];
-                else decode(qr[r]);
-            }
-        }
-        // the zero-fills issued past the walk must land before the slots are reused
-        cp_async_wait<0>();
-        if (tail_row >= 0)
-            piece_row<K>(p, i, j, gc, tail_row, true, nullptr, lc, tq, gmask, leader);
-        if (head) piece_row<K>(p, i, j, gc, x1, false, acc, lc, tq, gmask, leader);
-        return true;
-    }
     const int nst = nb * SPB;
     // q[r]: batch b + r, b the batch being summed
     ItemBatch<K> q[K::DEPTH];
 #pragma unroll
     for (int r = 0; r < K::DEPTH; ++r) decode(q[r]);
     ItemBatch<K>& A = q[0];
-    ItemBatch<K>& B = q[1];
     // stage t of the walk lies in batch t / SPB; batch b, b+1, b+2 are A, B, C
     auto issue_lsu_stage = [&](int t, int b) {
         const int bt = t / SPB;
@@ -655,83 +460,57 @@ __device__ __forceinline__ bool walk_unit(const Problem& p, int i, int j, int cs
         for (int r = 0; r <= K::REL; ++r)
             if (bt == b + r) issue_lsu(t, q[r], ht);
     };
-    if constexpr (K::TMA) {
-        if (nst > 0) issue_tma(0, A, 0);
-    } else {
 #pragma unroll
-        for (int k = 0; k < K::NBUF - 1; ++k) {
-            if (k < nst) issue_lsu_stage(k, 0);
-            else cp_async_commit();   // empty group: the wait count stays NBUF-1
-        }
+    for (int k = 0; k < K::NBUF - 1; ++k) {
+        if (k < nst) issue_lsu_stage(k, 0);
+        else cp_async_commit();   // empty group: the wait count stays NBUF-1
     }
 #pragma unroll 1
     for (int t = 0; t < nst; ++t) {
         const int h = SPB == 1 ? 0 : (t & (SPB - 1));
-        if constexpr (K::TMA) {
-            if (t + 1 < nst) {
-                if (SPB > 1 && h + 1 < SPB) issue_tma(t + 1, A, h + 1);
-                else issue_tma(t + 1, B, 0);
-            }
-            if (!consume_tma(t, A, h)) {
-                // a bulk copy never arrived: report, wait (bounded) for the
-                // other stage still in flight, and stop this warp
-                if (lane == 0) atomicCAS(p.status, 0, SPMM_ERR_TIMEOUT);
-                if (t + 1 < nst) {
-                    const uint32_t b1 = (uint32_t)((t + 1) & 1);
-                    mbar_wait_bounded(bar0 + 8u * b1, (phases >> b1) & 1u);
-                }
-                return false;
-            }
-        } else {
-            const int tn = t + K::NBUF - 1;
-            if (tn < nst) issue_lsu_stage(tn, t / SPB);
-            else cp_async_commit();
-            cp_async_wait<K::NBUF - 1>();
-            consume_lsu(t, A, h);
-        }
+        const int tn = t + K::NBUF - 1;
+        if (tn < nst) issue_lsu_stage(tn, t / SPB);
+        else cp_async_commit();
+        cp_async_wait<K::NBUF - 1>();
+        consume_lsu(t, A, h);
         if (h == SPB - 1) {
 #pragma unroll
             for (int r = 0; r + 1 < K::DEPTH; ++r) q[r] = q[r + 1];
             decode(q[K::DEPTH - 1]);
         }
     }
-    if (tail_row >= 0) piece_row<K>(p, i, j, gc, tail_row, true, nullptr, lc, tq, gmask, leader);
-    if (head) piece_row<K>(p, i, j, gc, x1, false, acc, lc, tq, gmask, leader);
-    return true;
+    if constexpr (DEFER) {
+        if (head) store_slot<K>(p, 2 * (int64_t)gc + 1, acc, lc);
+    } else {
+        if (tail_row >= 0)
+            piece_row<K>(p, i, j, gc, tail_row, true, nullptr, lc, tq, gmask, leader);
+        if (head) piece_row<K>(p, i, j, gc, x1, false, acc, lc, tq, gmask, leader);
+    }
 }
 
-// Per-warp set-up of the staging region (stage_bytes per warp) and its
-// mbarriers; returns the warp's staging base and sets bar0.
+// The warp's staging region (stage_bytes per warp, after 16 reserved bytes per
+// warp at the start of the CTA's dynamic shared memory).
 template <class K>
-__device__ __forceinline__ uint32_t warp_staging(int lane, uint32_t& bar0,
-                                                 int stage_bytes = K::STAGE_BYTES) {
+__device__ __forceinline__ uint32_t warp_staging(int stage_bytes = K::STAGE_BYTES) {
     const int warps = blockDim.x >> 5;
     const int w = threadIdx.x >> 5;
     const uint32_t smem = (uint32_t)__cvta_generic_to_shared(spmm_dyn_smem);
-    bar0 = smem + (uint32_t)(w * 16);
-    if (K::TMA) {
-        if (lane == 0) {
-            mbar_init(bar0, 1);
-            mbar_init(bar0 + 8, 1);
-            mbar_init_fence();
-        }
-        __syncwarp();
-    }
     return smem + (uint32_t)(warps * 16 + w * stage_bytes);
 }
 
 // The persistent kernel: each warp is an independent worker (see
 // persistent_schedule for the reservation order and the optional trace).
+// Split rows are left in workspace slots for split_row_fixup.
 template <class TA, class TB, int LPN, int VPL>
 __global__ void __launch_bounds__(256, (KCfg<TA, TB, LPN, VPL>::MINB))
 spmm_csr_persistent(const Problem p, int flags) {
     using K = KCfg<TA, TB, LPN, VPL>;
     const int lane = threadIdx.x & 31;
-    uint32_t bar0 = 0, phases = 0;
-    const uint32_t wbase = warp_staging<K>(lane, bar0);
+    const uint32_t wbase = warp_staging<K>();
     persistent_schedule<K::G>(p, flags, [&](int i, int j, int cs) {
         const LaneCols<K::VPL> lc = lane_cols<K, K::VPL, K::LPN>(p, j, lane % K::LPN);
-        return walk_unit<K>(p, i, j, cs, lc, lane, wbase, bar0, phases);
+        walk_unit<K, true>(p, i, j, cs, lc, lane, wbase);
+        return true;
     });
 }
 
