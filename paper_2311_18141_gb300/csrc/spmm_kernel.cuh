@@ -47,6 +47,9 @@
 #ifndef SPMM_STAGE_ITEMS
 #define SPMM_STAGE_ITEMS 8 // items per lane group in one stage (of one 16-byte vector each)
 #endif
+#ifndef SPMM_WALK_UNROLL
+#define SPMM_WALK_UNROLL 2 // stages per iteration of the walk loop
+#endif
 
 namespace spmm {
 
@@ -82,6 +85,9 @@ struct KCfg {
     static constexpr int DEPTH = REL + 2;
     // resident CTAs per SM the register budget targets
     static constexpr int MINB = (LPN <= 8 && VPL == 1) ? SPMM_MINBLOCKS_NARROW : SPMM_MINBLOCKS;
+    // stages per iteration of the walk loop: two where the accumulators and
+    // decoded batches leave room in the register budget (no spills)
+    static constexpr int UNROLL = (VPL == 1 && IPL <= 2) ? SPMM_WALK_UNROLL : 1;
     static_assert(DEPTH <= 8, "at most eight decoded batches");
     static_assert(SPB == 1 || IPL == 1, "split batches need one item per lane");
 };
@@ -252,6 +258,50 @@ __device__ __forceinline__ void piece_row(const Problem& p, int i, int j, int gc
     store_vecs<K, K::VPL, K::LPN>(p, r, sum, lc);
 }
 
+// Row end, stored without divergent branches: every lane of the warp runs
+// this; lanes whose group ends a row here (`mine`) store, the others are
+// predicated off.  A tail piece (`to_slot`) goes raw to workspace slot 2*gc,
+// a whole row to C as beta*C + a_scale*acc.
+template <class K>
+__device__ __forceinline__ void store_row_pred(const Problem& p, int row, bool mine,
+                                               bool to_slot, int gc, const float2* acc,
+                                               const LaneCols<K::VPL>& lc) {
+    const bool to_c = mine && !to_slot;
+    const bool scaled = p.a_scale != nullptr;
+    float sa = 1.0f;
+    if (scaled && to_c) sa = __ldg(p.a_scale + row);
+    float* dst = to_slot ? p.slots + 2 * (int64_t)gc * p.N + lc.c_off
+                         : reinterpret_cast<float*>(reinterpret_cast<char*>(lc.c) +
+                                                    (uint64_t)(uint32_t)row * lc.ldc_bytes);
+    const float beta = to_slot ? 0.0f : p.beta;
+#pragma unroll
+    for (int q = 0; q < K::VPL; ++q) {
+        const bool st = mine && ((lc.vmask >> q) & 1u);
+#pragma unroll
+        for (int h = 0; h < K::EPV / 4; ++h) {
+            float* d = dst + q * K::LPN * K::EPV + h * 4;
+            const float2 lo = acc[q * (K::EPV / 2) + 2 * h];
+            const float2 hi = acc[q * (K::EPV / 2) + 2 * h + 1];
+            float4 o = make_float4(lo.x, lo.y, hi.x, hi.y);
+            if (scaled) {
+                o.x *= sa;
+                o.y *= sa;
+                o.z *= sa;
+                o.w *= sa;
+            }
+            if (p.beta != 0.0f) {
+                float4 old = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                if (st && to_c) old = __ldcg(reinterpret_cast<const float4*>(d));
+                o.x = fmaf(beta, old.x, o.x);
+                o.y = fmaf(beta, old.y, o.y);
+                o.z = fmaf(beta, old.z, o.z);
+                o.w = fmaf(beta, old.w, o.w);
+            }
+            if (st) st_cs_f4(d, o);
+        }
+    }
+}
+
 template <int BITS>
 __host__ __device__ constexpr uint32_t low_bits() {
     return BITS >= 32 ? 0xffffffffu : ((1u << BITS) - 1u);
@@ -393,14 +443,19 @@ __device__ __forceinline__ void walk_unit(const Problem& p, int i, int j, int cs
         const float2 a2 = make_float2(a, a);
 #pragma unroll
         for (int q = 0; q < VPL; ++q) fma_vec<typename K::TB>(acc + q * (K::EPV / 2), a2, v[q]);
-        // the warp-uniform test skips the per-group test (and its divergent
-        // branch) on the items where no group of the warp ends a row
-        if (((X.any_end >> tt) & 1u) && ((X.ends >> tt) & 1u)) {
-            const int row = cur_row++;
-            if (row == tail_row) store_slot<K>(p, 2 * (int64_t)gc, acc, lc);
-            else store_vecs<K, VPL, LPN>(p, row, acc, lc);
+        // the warp-uniform test skips the row-end code on the items where no
+        // group of the warp ends a row; where one does, the whole warp runs it,
+        // predicated, with no divergent branch
+        if ((X.any_end >> tt) & 1u) {
+            const bool mine = (X.ends >> tt) & 1u;
+            const int row = cur_row;
+            cur_row += mine ? 1 : 0;
+            store_row_pred<K>(p, row, mine, row == tail_row, gc, acc, lc);
 #pragma unroll
-            for (int q = 0; q < K::NE / 2; ++q) acc[q] = make_float2(0.0f, 0.0f);
+            for (int q = 0; q < K::NE / 2; ++q) {
+                acc[q].x = mine ? 0.0f : acc[q].x;
+                acc[q].y = mine ? 0.0f : acc[q].y;
+            }
         }
     };
     // value of item tt of stage h, from the lane that decoded it
@@ -465,12 +520,18 @@ __device__ __forceinline__ void walk_unit(const Problem& p, int i, int j, int cs
         if (k < nst) issue_lsu_stage(k, 0);
         else cp_async_commit();   // empty group: the wait count stays NBUF-1
     }
-#pragma unroll 1
+    constexpr int kUnroll = K::UNROLL;
+#pragma unroll kUnroll
     for (int t = 0; t < nst; ++t) {
         const int h = SPB == 1 ? 0 : (t & (SPB - 1));
         const int tn = t + K::NBUF - 1;
-        if (tn < nst) issue_lsu_stage(tn, t / SPB);
-        else cp_async_commit();
+        if (tn < nst) {
+            // one stage per batch: stage tn is batch tn, q[NBUF-1]
+            if constexpr (SPB == 1) issue_lsu(tn, q[K::NBUF - 1], 0);
+            else issue_lsu_stage(tn, t / SPB);
+        } else {
+            cp_async_commit();
+        }
         cp_async_wait<K::NBUF - 1>();
         consume_lsu(t, A, h);
         if (h == SPB - 1) {

@@ -32,5 +32,5 @@ def test_bench_line_carries_the_contract():
     e = d["e2e"]
     assert e["value"] > 0 and e["h2d_bytes_per_step"] > 0 and e["d2h_bytes_per_step"] > 0
     assert e["value"] < d["value"]       # copies inside the timed region cost time
-    assert d["gpu_launches"] == 5
+    assert d["gpu_launches"] == 10     # per step: the product and the split-row sum
     assert d["config"]["workload"] == "rmat-s14-ef16-n128-fp32-grid16x4"
