@@ -20,6 +20,8 @@ struct spmm_plan_s {
     int32_t* bnd_row;
     int32_t* bnd_nnz;
     uint32_t* ends;       // row-end bitmap over the merge items
+    int4* split;          // rows cut by a chunk boundary (see plan_build)
+    int32_t* n_split;
     spmm_trace_record* trace;   // caller-owned per-warp trace records (null: off)
     int32_t trace_max;
 };
@@ -212,12 +214,13 @@ int spmm_plan_create(spmm_plan* plan, const int32_t* A_rowptr, int64_t M, int64_
     const size_t arrays = plan_array_bytes(tile_rows, p->cap);
     const size_t bytes = arrays + plan_ends_bytes(M + nnz);
     if (cudaMalloc(&p->mem, bytes) != cudaSuccess) { free(p); return SPMM_ERR_CUDA; }
-    plan_carve(p->mem, tile_rows, p->cap, &p->blk_base, &p->bnd_row, &p->bnd_nnz);
+    plan_carve(p->mem, tile_rows, p->cap, &p->blk_base, &p->bnd_row, &p->bnd_nnz, &p->split,
+               &p->n_split);
     p->ends = reinterpret_cast<uint32_t*>(static_cast<char*>(p->mem) + arrays);
     cudaError_t e = plan_build_ends(A_rowptr, M, M + nnz, p->ends, (cudaStream_t)stream);
     if (e == cudaSuccess)
         e = plan_build(A_rowptr, M, p->TR, p->RB, p->D, p->cap, p->blk_base, p->bnd_row,
-                               p->bnd_nnz, (cudaStream_t)stream);
+                       p->bnd_nnz, p->split, p->n_split, (cudaStream_t)stream);
     if (e != cudaSuccess) { cudaFree(p->mem); free(p); return SPMM_ERR_CUDA; }
     *plan = p;
     return SPMM_OK;
@@ -328,7 +331,8 @@ int spmm_csr(const int32_t* A_rowptr, const int32_t* A_colind, const void* A_val
     char* ws = static_cast<char*>(workspace);
     int32_t TR = tile_rows, TC = tile_cols, RB, D;
     int64_t cap;
-    int32_t *blk_base, *bnd_row, *bnd_nnz;
+    int32_t *blk_base, *bnd_row, *bnd_nnz, *n_split;
+    int4* split;
     uint32_t* ends;
     spmm_tuning tun;
     if (plan) {
@@ -338,6 +342,7 @@ int spmm_csr(const int32_t* A_rowptr, const int32_t* A_colind, const void* A_val
         RB = plan->RB; D = plan->D; cap = plan->cap;
         blk_base = plan->blk_base; bnd_row = plan->bnd_row; bnd_nnz = plan->bnd_nnz;
         ends = plan->ends;
+        split = plan->split; n_split = plan->n_split;
         tun = plan->tuning;
     } else {
         resolve_tuning(nullptr, &tun);
@@ -350,10 +355,11 @@ int spmm_csr(const int32_t* A_rowptr, const int32_t* A_colind, const void* A_val
         const size_t pb = pa + plan_ends_bytes(M + nnz);
         const Scratch sc = scratch_layout(TR, TC, cap, N);
         if (workspace_bytes < pb + sc.total) return SPMM_ERR_WORKSPACE;
-        plan_carve(ws + sc.total, TR, cap, &blk_base, &bnd_row, &bnd_nnz);
+        plan_carve(ws + sc.total, TR, cap, &blk_base, &bnd_row, &bnd_nnz, &split, &n_split);
         ends = reinterpret_cast<uint32_t*>(ws + sc.total + pa);
         if (plan_build_ends(A_rowptr, M, M + nnz, ends, s) != cudaSuccess ||
-            plan_build(A_rowptr, M, TR, RB, D, cap, blk_base, bnd_row, bnd_nnz, s) != cudaSuccess)
+            plan_build(A_rowptr, M, TR, RB, D, cap, blk_base, bnd_row, bnd_nnz, split, n_split,
+                       s) != cudaSuccess)
             return SPMM_ERR_CUDA;
         workspace_bytes -= pb;
     }
@@ -367,6 +373,7 @@ int spmm_csr(const int32_t* A_rowptr, const int32_t* A_colind, const void* A_val
     p.M = (int32_t)M; p.N = (int32_t)N; p.a_dtype = a_dtype; p.beta = beta;
     p.TR = TR; p.TC = TC; p.RB = RB; p.W = (int32_t)W; p.D = D;
     p.blk_base = blk_base; p.bnd_row = bnd_row; p.bnd_nnz = bnd_nnz; p.ends = ends;
+    p.split = split; p.n_split = n_split;
     p.status = reinterpret_cast<int32_t*>(ws);
     p.tile_ctr = reinterpret_cast<int32_t*>(ws + sc.counters_off);
     p.piece_cnt = p.tile_ctr + (size_t)TR * TC;

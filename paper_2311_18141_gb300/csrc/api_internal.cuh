@@ -16,9 +16,9 @@ int plan_view(spmm_plan plan, int64_t M, int64_t K, int64_t nnz, int64_t N, int3
               int32_t* TC, int32_t* RB, int32_t* D, int64_t* cap, int32_t** blk_base,
               int32_t** bnd_row, int32_t** bnd_nnz);
 // Sum the split rows of a staged product (left in workspace slots by
-// spmm_csr_persistent) into C; `max_boundaries` bounds the plan's boundaries
-// (chunk capacity + TR).  Enqueued on `s` after the product.
-cudaError_t launch_split_row_fixup(const Problem& p, int64_t max_boundaries, cudaStream_t s);
+// spmm_csr_persistent) into C; `max_rows` bounds the length of the plan's
+// split-row list (chunk capacity + TR).  Enqueued on `s` after the product.
+cudaError_t launch_split_row_fixup(const Problem& p, int64_t max_rows, cudaStream_t s);
 // Shape of a plan (any output may be null).
 int plan_shape(spmm_plan plan, int64_t* M, int64_t* K, int64_t* nnz, int64_t* N, int32_t* TR,
                int32_t* TC);

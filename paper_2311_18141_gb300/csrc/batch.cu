@@ -141,15 +141,16 @@ int batch_build(spmm_batch b, cudaStream_t s) {
         BatchEntry& e = b->h_table[k];
         memset(&e, 0, sizeof(e));
         Problem& p = e.p;
-        int32_t *blk_base, *bnd_row, *bnd_nnz;
+        int32_t *blk_base, *bnd_row, *bnd_nnz, *n_split;
+        int4* split;
         plan_carve(static_cast<char*>(b->plan_mem) + plan_off[q], b->TR[q], b->cap[q], &blk_base,
-                   &bnd_row, &bnd_nnz);
+                   &bnd_row, &bnd_nnz, &split, &n_split);
         const int32_t RB = (int32_t)std::max<int64_t>(1, (P.M + b->TR[q] - 1) / b->TR[q]);
         uint32_t* ends = reinterpret_cast<uint32_t*>(static_cast<char*>(b->plan_mem) + plan_off[q] +
                                                      plan_array_bytes(b->TR[q], b->cap[q]));
         if (plan_build_ends(P.rowptr, P.M, P.M + P.nnz, ends, s) != cudaSuccess ||
             plan_build(P.rowptr, P.M, b->TR[q], RB, b->D[q], b->cap[q], blk_base, bnd_row, bnd_nnz,
-                       s) != cudaSuccess)
+                       split, n_split, s) != cudaSuccess)
             return SPMM_ERR_CUDA;
         p.rowptr = P.rowptr; p.colind = P.colind; p.vals = P.vals; p.a_scale = P.a_scale;
         p.B = P.B; p.b_scale = P.b_scale; p.C = P.C; p.ldb = P.ldb; p.ldc = P.ldc;
@@ -157,6 +158,7 @@ int batch_build(spmm_batch b, cudaStream_t s) {
         p.TR = b->TR[q]; p.TC = b->TC[q]; p.RB = RB;
         p.W = (int32_t)column_block_width(P.N, b->TC[q], b->b_dtype); p.D = b->D[q];
         p.blk_base = blk_base; p.bnd_row = bnd_row; p.bnd_nnz = bnd_nnz; p.ends = ends;
+        p.split = split; p.n_split = n_split;
         e.piece_off = piece_off[q];
         e.slot_off = slot_off[q];
         e.lpn = b->lpn[q];

@@ -333,6 +333,8 @@ struct Problem {
     const int32_t* bnd_row;   // boundary (row, nnz) at index blk_base[i] + i + c
     const int32_t* bnd_nnz;
     const uint32_t* ends;     // row-end bitmap over the merge items (see plan_ends_bytes)
+    const int4* split;        // rows cut by a chunk boundary: {row, first chunk, last chunk, 0}
+    const int32_t* n_split;   // how many entries of `split` the plan wrote
     // per-call scratch
     int32_t* tile_ctr;        // [TR*TC]
     int32_t* piece_cnt;       // [chunks*TC]

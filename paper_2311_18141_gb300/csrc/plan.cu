@@ -57,7 +57,8 @@ plan_blocks_kernel(const int32_t* __restrict__ rowptr, int M, int TR, int RB, in
 // c = b - blk_base[i] - i (0 <= c <= chunks of block i).
 __global__ void plan_bounds_kernel(const int32_t* __restrict__ rowptr, int M, int TR, int RB,
                                    int D, const int32_t* __restrict__ blk_base, int64_t cap,
-                                   int32_t* __restrict__ bnd_row, int32_t* __restrict__ bnd_nnz) {
+                                   int32_t* __restrict__ bnd_row, int32_t* __restrict__ bnd_nnz,
+                                   int4* __restrict__ split, int32_t* __restrict__ n_split) {
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= cap) return;
     const int64_t total = (int64_t)blk_base[TR] + TR;
@@ -95,6 +96,18 @@ __global__ void plan_bounds_kernel(const int32_t* __restrict__ rowptr, int M, in
         const int64_t rs = (int64_t)rowptr[row_lo + xl] - nnz_lo;
         const int64_t re = (int64_t)rowptr[row_lo + xl + 1] - nnz_lo;
         if (y > rs && 8 * (re - rs + 1) < D) y = rs;
+        // Still inside the row: the row is cut.  The first boundary inside it
+        // (the one that ends the chunk where the row's first item lies) lists
+        // it, with the chunks of its first item and of its end.
+        if (y > rs && c >= 1) {
+            const int64_t ca = (xl + rs) / D;
+            if (c == ca + 1) {
+                const int64_t cb = (xl + re) / D;
+                const int k = atomicAdd(n_split, 1);
+                split[k] = make_int4(row_lo + (int)xl, blk_base[i] + (int)ca,
+                                     blk_base[i] + (int)cb, 0);
+            }
+        }
     }
     bnd_row[b] = (int32_t)(row_lo + xl);
     bnd_nnz[b] = (int32_t)(nnz_lo + y);
@@ -150,30 +163,37 @@ int plan_default_groups(int64_t N, int32_t TC) {
 size_t plan_array_bytes(int32_t TR, int64_t cap) {
     size_t a = ((size_t)(TR + 1) * 4 + 255) / 256 * 256;
     size_t b = ((size_t)(cap + TR) * 4 + 255) / 256 * 256;
-    return a + 2 * b;
+    size_t l = ((size_t)(cap + TR) * 16 + 255) / 256 * 256;
+    return a + 2 * b + l + 256;
 }
 
 void plan_carve(void* base, int32_t TR, int64_t cap, int32_t** blk_base, int32_t** bnd_row,
-                int32_t** bnd_nnz) {
+                int32_t** bnd_nnz, int4** split, int32_t** n_split) {
     char* p = static_cast<char*>(base);
     size_t a = ((size_t)(TR + 1) * 4 + 255) / 256 * 256;
     size_t b = ((size_t)(cap + TR) * 4 + 255) / 256 * 256;
+    size_t l = ((size_t)(cap + TR) * 16 + 255) / 256 * 256;
     *blk_base = reinterpret_cast<int32_t*>(p);
     *bnd_row = reinterpret_cast<int32_t*>(p + a);
     *bnd_nnz = reinterpret_cast<int32_t*>(p + a + b);
+    *split = reinterpret_cast<int4*>(p + a + 2 * b);
+    *n_split = reinterpret_cast<int32_t*>(p + a + 2 * b + l);
 }
 
 cudaError_t plan_build(const int32_t* rowptr, int64_t M, int32_t TR, int32_t RB, int32_t D,
                        int64_t cap, int32_t* blk_base, int32_t* bnd_row, int32_t* bnd_nnz,
-                       cudaStream_t s) {
+                       int4* split, int32_t* n_split, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(n_split, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
     plan_blocks_kernel<<<1, 1024, 0, s>>>(rowptr, (int)M, TR, RB, D, blk_base);
-    cudaError_t e = cudaGetLastError();
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int64_t slots = cap + TR;
     const int threads = 256;
     const int64_t blocks = ceil_div(slots, threads);
     plan_bounds_kernel<<<(unsigned)blocks, threads, 0, s>>>(rowptr, (int)M, TR, RB, D, blk_base,
-                                                           slots, bnd_row, bnd_nnz);
+                                                           slots, bnd_row, bnd_nnz, split,
+                                                           n_split);
     return cudaGetLastError();
 }
 

@@ -400,8 +400,11 @@ extern "C" int spmm_sddmm_csr(const int32_t* A_rowptr, const int32_t* A_colind, 
         // layout [status, counter (256 B)][plan arrays]
         const size_t pb = plan_array_bytes(TR, cap);
         if (workspace_bytes < pb + 256) return SPMM_ERR_WORKSPACE;
-        plan_carve(ws + 256, TR, cap, &blk_base, &bnd_row, &bnd_nnz);
-        if (plan_build(A_rowptr, M, TR, RB, D, cap, blk_base, bnd_row, bnd_nnz, st) != cudaSuccess)
+        int4* split;
+        int32_t* n_split;
+        plan_carve(ws + 256, TR, cap, &blk_base, &bnd_row, &bnd_nnz, &split, &n_split);
+        if (plan_build(A_rowptr, M, TR, RB, D, cap, blk_base, bnd_row, bnd_nnz, split, n_split,
+                       st) != cudaSuccess)
             return SPMM_ERR_CUDA;
         workspace_bytes -= pb;
     }

@@ -10,16 +10,17 @@
 //   * A warp is G = 32/LPN lane groups; LPN lanes hold one column block of a
 //     B row in 16-byte vectors.  A work unit is G consecutive sub-chunks of
 //     one tile, one per group.
-//   * Each tile has a counter; a warp reserves the next unit of a tile with
-//     one atomicAdd (the fetch-and-add of Algorithm 3).  Warps start on
-//     staggered home tiles (the iteration offset of Section 3.3) and, when a
-//     tile runs dry, move on to other tiles, same tile row first (order 0) or
-//     same tile column first (order 1): the locality-aware stealing order.
+//   * Each tile (or, in the default interleaved order, each tile row) has a
+//     counter; a warp reserves the next unit with one atomicAdd (the
+//     fetch-and-add of Algorithm 3).  Warps start on staggered home tiles
+//     (the iteration offset of Section 3.3) and, when theirs runs dry, move
+//     on to others in a locality-aware stealing order (schedule.cuh).
 //   * A row cut by a sub-chunk boundary yields one partial vector per
-//     sub-chunk.  Each partial goes to a workspace slot; a per-(row, column
-//     block) counter tells the group that finishes last, which sums the
-//     partials in sub-chunk order and writes C.  No atomics touch C and the
-//     result is reproducible.
+//     sub-chunk, each left in a workspace slot.  After the persistent launch
+//     split_row_fixup sums each such row's partials (the plan lists the rows)
+//     in sub-chunk order and writes C; in the batched kernel a
+//     per-(row, column block) counter tells the group that finishes last to
+//     do the same.  No atomics touch C and the result is reproducible.
 //
 // Inside a unit every group walks its own sub-chunk item by item: a nonzero
 // item gathers the B row segment and accumulates it, a row-end item writes
@@ -86,8 +87,10 @@ struct KCfg {
     // resident CTAs per SM the register budget targets
     static constexpr int MINB = (LPN <= 8 && VPL == 1) ? SPMM_MINBLOCKS_NARROW : SPMM_MINBLOCKS;
     // stages per iteration of the walk loop: two where the accumulators and
-    // decoded batches leave room in the register budget (no spills)
-    static constexpr int UNROLL = (VPL == 1 && IPL <= 2) ? SPMM_WALK_UNROLL : 1;
+    // decoded batches leave room in the register budget (no spills) and the
+    // per-item conversion is short (B types of at most 8 elements per vector;
+    // the E4M3 loop body, unrolled, ran 2.4x slower)
+    static constexpr int UNROLL = (VPL == 1 && IPL <= 2 && EPV <= 8) ? SPMM_WALK_UNROLL : 1;
     static_assert(DEPTH <= 8, "at most eight decoded batches");
     static_assert(SPB == 1 || IPL == 1, "split batches need one item per lane");
 };
