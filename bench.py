@@ -898,7 +898,8 @@ def run_gather(args):
     benchmark's 16 x 4 grid (128-byte segments) and 16 x 1 (512 bytes), on the
     matrix's own column stream, on uniform random columns (no reuse: DRAM
     bound) and on columns below 60,000 (30 MB of B rows: L2-resident), next to
-    the full SpMM at the same grid.  The gathered bytes are nnz * N * 4."""
+    the full SpMM at the same grid, on the matrix's columns and on the
+    L2-resident ones.  The gathered bytes are nnz * N * 4."""
     import torch
     from paper_2311_18141_gb300 import binding
     dev = torch.device("cuda")
@@ -960,6 +961,12 @@ def run_gather(args):
         ms = timed(lambda: binding.spmm_csr(A.rowptr, A.colind, A.vals, B, C, M, K, N, nnz,
                                             plan=plan, ws=ws, stream=stream))
         row["spmm_ms"] = ms
+        # the same product on the L2-resident column stream: the kernel's SM
+        # side with B's misses taken away
+        ci_l2 = streams["l2_resident"]
+        row["spmm_l2_resident_ms"] = timed(
+            lambda: binding.spmm_csr(A.rowptr, ci_l2, A.vals, B, C, M, K, N, nnz, plan=plan,
+                                     ws=ws, stream=stream))
         row["spmm_over_gather_floor"] = ms / row["rmat"]["ms"]
         row["spmm_hbm_frac_at_gather_floor"] = (min_bytes(M, K, N, nnz) /
                                                 (row["rmat"]["ms"] * 1e-3) / 1e9 /
