@@ -143,8 +143,18 @@ int64_t plan_chunk_cap(int64_t M, int64_t nnz, int32_t TR, int32_t D) {
 int32_t plan_default_chunk(int64_t M, int64_t nnz, int32_t TC, int sms, int groups) {
     const int64_t nwarps = (int64_t)(sms > 0 ? sms : 148) * 32;
     if (groups < 1) groups = 1;
+    const int64_t work = (M + nnz) * (int64_t)TC;
     // about 16 units per warp of the full grid, a unit being `groups` chunks
-    int64_t d = ceil_div((M + nnz) * (int64_t)TC, 16 * nwarps * groups);
+    int64_t d = ceil_div(work, 16 * nwarps * groups);
+    // Longer chunks, up to 16 mean rows (M + nnz) / M, while the grid keeps at
+    // least 4 units per warp: a boundary cuts only rows of D/8 items or more,
+    // and every cut row costs its pieces' slot stores and the fix-up's reads.
+    if (M > 0) {
+        const int64_t rows16 = ceil_div(16 * (M + nnz), M);
+        const int64_t d4 = work / (4 * nwarps * groups);
+        const int64_t want = rows16 < d4 ? rows16 : d4;
+        if (want > d) d = want;
+    }
     if (d < 32) d = 32;   // small problems: enough units to spread over the SMs
     if (d > 16384) d = 16384;
     d = ceil_div(d, 32) * 32;

@@ -8,7 +8,8 @@ namespace spmm {
 
 // Upper bound on the number of chunks of all row blocks.
 int64_t plan_chunk_cap(int64_t M, int64_t nnz, int32_t TR, int32_t D);
-// Default merge-path items per chunk: about 16 units per resident warp.
+// Default merge-path items per chunk: about 16 units per warp of the grid, or
+// longer (up to 16 mean rows, keeping 4 units per warp) so that few rows are cut.
 int32_t plan_default_chunk(int64_t M, int64_t nnz, int32_t TC, int sms, int groups);
 // Lane groups per warp of the staged kernel's FP32 shape for N columns in TC
 // blocks (the default kernel).
