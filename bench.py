@@ -58,7 +58,7 @@ def parse():
                          "tiles handed out in turn)")
     ap.add_argument("--kernel", type=int, default=0,
                     help="spmm_tuning.kernel: 0 library default, 1 staged 16-byte kernel, "
-                         "2 32-byte-lane kernel")
+                         "2 32-byte-lane kernel, 3 warp-specialised staged kernel")
     ap.add_argument("--ksplit", type=int, default=0,
                     help="gather workload: also time the gathers in the orders of a K-split "
                          "3D grid with this many k-blocks")
@@ -109,7 +109,8 @@ def kernel_name(N, TC, esz=4, kernel=0, tag="TagF32", lanes=0):
     """The persistent kernel the library launches for FP32 A and B of element
     size `esz` (aligned torch tensors, dense strides): the staged kernel by
     default, the 32-byte-lane kernel when asked for (kernel 2) and a column
-    block is 2..32 whole 32-byte vectors."""
+    block is 2..32 whole 32-byte vectors, the warp-specialised kernel when
+    asked for (kernel 3) and a block is 8..32 16-byte vectors."""
     epv = 16 // esz
     w = -(-N // TC)
     w = -(-w // epv) * epv
@@ -126,6 +127,8 @@ def kernel_name(N, TC, esz=4, kernel=0, tag="TagF32", lanes=0):
             lpn *= 2
         if lanes in (2, 4) and nvec in (4, 8) and lpn == nvec and lanes < nvec and nvec // lanes <= 4:
             return f"spmm_csr_persistent<TagF32,{tag},{lanes},{nvec // lanes}>"
+        if kernel == 3 and lpn >= 8:
+            return f"spmm_csr_spec<TagF32,{tag},{lpn},1>"
         return f"spmm_csr_persistent<TagF32,{tag},{lpn},1>"
     return f"spmm_csr_persistent<TagF32,{tag},32,{2 if nvec <= 64 else 4}>"
 

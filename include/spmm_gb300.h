@@ -91,7 +91,12 @@ typedef struct spmm_tuning {
                               SPMM_KERNEL_WIDE (2): the 32-byte-lane register-gather
                               kernel, or SPMM_ERR_MISALIGNED when B, C, their strides
                               or the column blocks are not whole 32-byte vectors of
-                              2..32 vectors per block                                   */
+                              2..32 vectors per block;
+                              SPMM_KERNEL_SPEC (3): the warp-specialised staged kernel
+                              (producer warps decode and gather, consumer warps sum;
+                              FP32 A with FP32 or BF16 B, FP16 A with FP32, FP16 or
+                              BF16 B, column blocks of 8..32 16-byte vectors), else
+                              SPMM_ERR_UNSUPPORTED                                      */
     int32_t lanes_per_item; /* 0: the default, one 16-byte vector per lane (a column
                               block of 8 vectors is walked by 8 lanes); 2 or 4: a block
                               of 4 or 8 vectors is walked by that many lanes holding
@@ -103,6 +108,7 @@ typedef struct spmm_tuning {
 #define SPMM_KERNEL_AUTO 0
 #define SPMM_KERNEL_STAGED 1
 #define SPMM_KERNEL_WIDE 2
+#define SPMM_KERNEL_SPEC 3
 
 /* Human-readable name of a status code (static storage). */
 const char* spmm_status_string(int status);

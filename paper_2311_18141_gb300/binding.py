@@ -63,7 +63,7 @@ class spmm_tuning(ctypes.Structure):
 
 
 # spmm_tuning.kernel
-SPMM_KERNEL_AUTO, SPMM_KERNEL_STAGED, SPMM_KERNEL_WIDE = 0, 1, 2
+SPMM_KERNEL_AUTO, SPMM_KERNEL_STAGED, SPMM_KERNEL_WIDE, SPMM_KERNEL_SPEC = 0, 1, 2, 3
 
 
 class spmm_problem(ctypes.Structure):

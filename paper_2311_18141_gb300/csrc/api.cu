@@ -76,7 +76,7 @@ void resolve_tuning(const spmm_tuning* in, spmm_tuning* out) {
     if (out->ctas_per_sm < 0) out->ctas_per_sm = 0;
     if (out->tile_order < 0 || out->tile_order > 31) out->tile_order = 0;
     if (out->chunk_items < 0) out->chunk_items = 0;
-    if (out->kernel < SPMM_KERNEL_AUTO || out->kernel > SPMM_KERNEL_WIDE)
+    if (out->kernel < SPMM_KERNEL_AUTO || out->kernel > SPMM_KERNEL_SPEC)
         out->kernel = SPMM_KERNEL_AUTO;
     if (out->lanes_per_item != 2 && out->lanes_per_item != 4) out->lanes_per_item = 0;
 }
@@ -395,6 +395,12 @@ int spmm_csr(const int32_t* A_rowptr, const int32_t* A_colind, const void* A_val
         const WideLaunchFn fn = wide_launcher(a_dtype, b_dtype);
         if (!fn) return SPMM_ERR_UNSUPPORTED;
         e = fn(wlpn, wnv, p, o, s);
+    } else if (tun.kernel == SPMM_KERNEL_SPEC) {
+        const SpecLaunchFn fn = spec_launcher(a_dtype, b_dtype);
+        if (!fn || vpl != 1 || lpn < 8) return SPMM_ERR_UNSUPPORTED;
+        e = fn(lpn, p, o, s);
+        // like the staged kernel, it leaves split rows in the slots
+        if (e == cudaSuccess) e = launch_split_row_fixup(p, cap + TR, s);
     } else {
         const LaunchFn fn = spmm_launcher(a_dtype, b_dtype);
         if (!fn) return SPMM_ERR_UNSUPPORTED;

@@ -54,17 +54,19 @@ __device__ __forceinline__ void cp_async16(uint32_t smem_addr, const void* gptr,
                  :: "r"(smem_addr), "l"(gptr), "r"(src_bytes) : "memory");
 #endif
 }
-// The same copy with a predicate instead of a size: `skip` writes 16 zero
-// bytes and reads nothing.
-__device__ __forceinline__ void cp_async16_zero_if(uint32_t smem_addr, const void* gptr,
-                                                   bool skip) {
-    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t"
+// 16-byte cp.async that zero-fills instead of reading when `mask & bit` is
+// 0: the test is part of the asm (a constant `bit` folds into it), so no 0/1
+// value is formed first.
+__device__ __forceinline__ void cp_async16_if_set(uint32_t smem_addr, const void* gptr,
+                                                  uint32_t mask, uint32_t bit) {
+    asm volatile("{\n\t.reg .pred q;\n\t.reg .b32 t;\n\t"
+                 "and.b32 t, %2, %3;\n\tsetp.eq.b32 q, t, 0;\n\t"
 #if SPMM_CP_ASYNC_CA
                  "cp.async.ca.shared.global [%0], [%1], 16, q;\n\t}"
 #else
                  "cp.async.cg.shared.global [%0], [%1], 16, q;\n\t}"
 #endif
-                 :: "r"(smem_addr), "l"(gptr), "r"((int)skip) : "memory");
+                 :: "r"(smem_addr), "l"(gptr), "r"(mask), "r"(bit) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() {
     asm volatile("cp.async.commit_group;" ::: "memory");

@@ -25,6 +25,10 @@ using LaunchFn = cudaError_t (*)(int lpn, int vpl, const Problem& p, const Launc
 using WideLaunchFn = cudaError_t (*)(int lpn, int nv, const Problem& p, const LaunchOpts& o,
                                      cudaStream_t s);
 
+// Warp-specialised kernel: lpn lanes per item, one 16-byte vector per lane.
+using SpecLaunchFn = cudaError_t (*)(int lpn, const Problem& p, const LaunchOpts& o,
+                                     cudaStream_t s);
+
 struct BatchEntry;
 // Batched persistent launch of the products table[0 .. count) of lane shape
 // `lpn`: `ctas_per_sm` 0 = occupancy limit.
@@ -105,5 +109,7 @@ SPMM_DECLARE_LAUNCHER(e4m3, bf16) SPMM_DECLARE_LAUNCHER(e4m3, e4m3)
 LaunchFn spmm_launcher(int a_dtype, int b_dtype);
 WideLaunchFn wide_launcher(int a_dtype, int b_dtype);
 BatchLaunchFn batched_launcher(int a_dtype, int b_dtype);
+// the warp-specialised kernel's launcher, or null for the pairs it is not built for
+SpecLaunchFn spec_launcher(int a_dtype, int b_dtype);
 
 }  // namespace spmm

@@ -48,6 +48,9 @@
 #ifndef SPMM_STAGE_ITEMS
 #define SPMM_STAGE_ITEMS 8 // items per lane group in one stage (of one 16-byte vector each)
 #endif
+#ifndef SPMM_DECODE_EXTRA
+#define SPMM_DECODE_EXTRA 0 // batches decoded ahead beyond the two the stages need
+#endif
 #ifndef SPMM_WALK_UNROLL
 #define SPMM_WALK_UNROLL 2 // stages per iteration of the walk loop
 #endif
@@ -83,7 +86,7 @@ struct KCfg {
     // current one; one more batch is decoded so that its column indices load
     // a batch before their gathers issue
     static constexpr int REL = (SPB - 1 + NBUF - 1) / SPB;
-    static constexpr int DEPTH = REL + 2;
+    static constexpr int DEPTH = REL + 2 + SPMM_DECODE_EXTRA;
     // resident CTAs per SM the register budget targets
     static constexpr int MINB = (LPN <= 8 && VPL == 1) ? SPMM_MINBLOCKS_NARROW : SPMM_MINBLOCKS;
     // stages per iteration of the walk loop: two where the accumulators and
@@ -481,12 +484,11 @@ __device__ __forceinline__ void walk_unit(const Problem& p, int i, int j, int cs
                 tt = h * SS + s;
                 cc = __shfl_sync(kFull, X.col[0], tt, LPN);
             }
-            const bool skip = !((X.nz >> tt) & 1u);
             const char* rp = brow(lc, cc);
 #pragma unroll
             for (int q = 0; q < VPL; ++q)
-                cp_async16_zero_if(buf + (uint32_t)((s * VPL + q) * 32 * 16), rp + lc.qoff[q],
-                                   skip);
+                cp_async16_if_set(buf + (uint32_t)((s * VPL + q) * 32 * 16), rp + lc.qoff[q],
+                                  X.nz, 1u << tt);
         }
         cp_async_commit();
     };
