@@ -480,7 +480,7 @@ def run_ours(args):
         depth, best_ms = (2, e2e_ms) if e2e_ms <= serial_ms else (1, serial_ms)
         e2e = {"value": flops * world / (best_ms * 1e-3) / 1e9, "unit": "GFLOP/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": best_ms,
-               "steps": n_e2e, "pipelined": True, "api": f"spmm_host_pipe (depth {depth})",
+               "steps": n_e2e, "pipelined": depth > 1, "api": f"spmm_host_pipe (depth {depth})",
                "ms_per_step_by_depth": {"1": serial_ms, "2": e2e_ms}}
         del rp_h, ci_h, v_h, B_h, C_hs
 
