@@ -320,6 +320,9 @@ static int batch_enqueue(spmm_batch b, void* workspace, size_t bytes, cudaStream
                                  ws, counters + g, G.max_items, b->ctas_per_sm, s);
         if (e != cudaSuccess) return SPMM_ERR_CUDA;
     }
+    // the rows that chunk boundaries cut, summed from their slots
+    if (launch_split_row_fixup_batched(b->d_table, (int)b->count, ws, s) != cudaSuccess)
+        return SPMM_ERR_CUDA;
     return SPMM_OK;
 }
 

@@ -10,7 +10,9 @@
 // any other.  Within a group the host orders products by width, then by
 // decreasing work, so the largest are reserved first.  Each warp copies the
 // descriptor of the product it is working on into its own slot of shared
-// memory and runs the same unit code as the single-product kernel.  One shape
+// memory and runs the same unit code as the single-product kernel; the rows
+// that chunk boundaries cut are summed afterwards, for all products in one
+// launch (split_row_fixup_batched_kernel).  One shape
 // per kernel keeps its register count, and so its resident warps, those of the
 // single-product kernel.
 #pragma once
@@ -64,7 +66,7 @@ __device__ __forceinline__ void batch_unit(const Problem& p, int u, int j, int l
         }
         cs = gsc - p.blk_base[il];
     }
-    walk_unit<K, false>(p, il, j, cs, lc, lane, wbase);
+    walk_unit<K>(p, il, j, cs, lc, lane, wbase);
 }
 
 // The products of one lane shape (LPN lanes per column block) of a batch:

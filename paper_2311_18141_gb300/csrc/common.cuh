@@ -75,15 +75,6 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory");
 }
-// 16-byte shared load when `p`, else zeros (no access).
-__device__ __forceinline__ uint4 lds128_if(uint32_t smem_addr, bool p) {
-    uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %5, 0;\n\t"
-                 "@q ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];\n\t}"
-                 : "+r"(v.x), "+r"(v.y), "+r"(v.z), "+r"(v.w)
-                 : "r"(smem_addr), "r"((int)p));
-    return v;
-}
 
 // ---- mbarriers and bulk asynchronous copies (the TMA engine) ----
 // A bulk copy moves `bytes` (a multiple of 16, both addresses 16-byte

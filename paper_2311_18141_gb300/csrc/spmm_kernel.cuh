@@ -16,11 +16,10 @@
 //     (the iteration offset of Section 3.3) and, when theirs runs dry, move
 //     on to others in a locality-aware stealing order (schedule.cuh).
 //   * A row cut by a sub-chunk boundary yields one partial vector per
-//     sub-chunk, each left in a workspace slot.  After the persistent launch
-//     split_row_fixup sums each such row's partials (the plan lists the rows)
-//     in sub-chunk order and writes C; in the batched kernel a
-//     per-(row, column block) counter tells the group that finishes last to
-//     do the same.  No atomics touch C and the result is reproducible.
+//     sub-chunk, each left in a workspace slot.  After the persistent (or
+//     batched) launch split_row_fixup sums each such row's partials (the plan
+//     lists the rows) in sub-chunk order and writes C.  No atomics touch C and
+//     the result is reproducible.
 //
 // Inside a unit every group walks its own sub-chunk item by item: a nonzero
 // item gathers the B row segment and accumulates it, a row-end item writes
@@ -152,42 +151,6 @@ __device__ __forceinline__ const char* brow(const LaneCols<NV>& lc, int col) {
     return lc.b + (uint64_t)(uint32_t)col * lc.ldb_bytes;
 }
 
-// C[r] = beta*C[r] + a_scale[r]*acc for the NV vectors of this lane (stride
-// STRIDE lanes).  No warp-synchronous operation: callable by one group alone.
-template <class K, int NV, int STRIDE>
-__device__ __forceinline__ void store_vecs(const Problem& p, int64_t r, const float2* acc,
-                                           const LaneCols<NV>& lc) {
-    const bool scaled = p.a_scale != nullptr;
-    const float sa = scaled ? __ldg(p.a_scale + r) : 1.0f;
-    float* dst = reinterpret_cast<float*>(reinterpret_cast<char*>(lc.c) +
-                                          (uint64_t)(uint32_t)r * lc.ldc_bytes);
-#pragma unroll
-    for (int q = 0; q < NV; ++q) {
-        if (!((lc.vmask >> q) & 1u)) continue;
-#pragma unroll
-        for (int h = 0; h < K::EPV / 4; ++h) {
-            float* d = dst + q * STRIDE * K::EPV + h * 4;
-            const float2 lo = acc[q * (K::EPV / 2) + 2 * h];
-            const float2 hi = acc[q * (K::EPV / 2) + 2 * h + 1];
-            float4 o = make_float4(lo.x, lo.y, hi.x, hi.y);
-            if (scaled) {
-                o.x *= sa;
-                o.y *= sa;
-                o.z *= sa;
-                o.w *= sa;
-            }
-            if (p.beta != 0.0f) {
-                const float4 old = __ldcg(reinterpret_cast<const float4*>(d));
-                o.x = fmaf(p.beta, old.x, o.x);
-                o.y = fmaf(p.beta, old.y, o.y);
-                o.z = fmaf(p.beta, old.z, o.z);
-                o.w = fmaf(p.beta, old.w, o.w);
-            }
-            st_cs_f4(d, o);
-        }
-    }
-}
-
 // Raw partial vector of this lane into workspace slot `slot`.
 template <class K>
 __device__ __forceinline__ void store_slot(const Problem& p, int64_t slot, const float2* acc,
@@ -203,65 +166,6 @@ __device__ __forceinline__ void store_slot(const Problem& p, int64_t slot, const
             st_cg_f4(dst + q * K::LPN * K::EPV + h * 4, make_float4(lo.x, lo.y, hi.x, hi.y));
         }
     }
-}
-
-// Partial row r of global sub-chunk gc: the group's piece goes to its slot
-// (the row's tail piece to slot 2*gc, its head piece to 2*gc+1; `acc` is
-// null when the caller has stored it already), and if it is the last piece of
-// the row to arrive, the group sums all pieces in sub-chunk order and writes
-// C.  Called by the LPN lanes of one group (mask gmask, first lane `leader`);
-// other groups may be elsewhere.
-template <class K>
-__device__ __forceinline__ void piece_row(const Problem& p, int i, int j, int gc, int r,
-                                          bool tail, const float2* acc,
-                                          const LaneCols<K::VPL>& lc, int tq,
-                                          unsigned gmask, int leader) {
-    if (acc) store_slot<K>(p, 2 * (int64_t)gc + (tail ? 0 : 1), acc, lc);
-    // __syncwarp orders the group's slot stores before the leader's release;
-    // the acq_rel atomic publishes them and, for the last piece, acquires the
-    // other pieces' stores, which the second __syncwarp extends to the group.
-    __syncwarp(gmask);
-    int ca = 0, cb = 0, last = 0;
-    if (tq == 0) {
-        const int row_lo = i * p.RB;
-        const int nnz_lo = __ldg(p.rowptr + row_lo);
-        const int rstart = __ldg(p.rowptr + r);
-        const int rend = __ldg(p.rowptr + r + 1);
-        ca = (int)(((int64_t)(r - row_lo) + (rstart - nnz_lo)) / p.D);
-        cb = (int)(((int64_t)(r - row_lo) + (rend - nnz_lo)) / p.D);
-        const int base = p.blk_base[i];
-        int* cnt = p.piece_cnt + (int64_t)(base + cb) * p.TC + j;
-        const int old = atom_add_acq_rel(cnt, 1);
-        last = (old == cb - ca);
-        ca += base;
-        cb += base;
-    }
-    __syncwarp(gmask);
-    last = __shfl_sync(gmask, last, leader);
-    if (!last) return;
-    ca = __shfl_sync(gmask, ca, leader);
-    cb = __shfl_sync(gmask, cb, leader);
-    float2 sum[K::NE / 2];
-#pragma unroll
-    for (int e = 0; e < K::NE / 2; ++e) sum[e] = make_float2(0.0f, 0.0f);
-    for (int cc = ca; cc <= cb; ++cc) {
-        const int64_t s2 = 2 * (int64_t)cc + (cc == cb ? 0 : 1);
-        const float* src = p.slots + s2 * p.N + lc.c_off;
-#pragma unroll
-        for (int q = 0; q < K::VPL; ++q) {
-            if (!((lc.vmask >> q) & 1u)) continue;
-#pragma unroll
-            for (int h = 0; h < K::EPV / 4; ++h) {
-                const float4 v = ld_cg_f4(src + q * K::LPN * K::EPV + h * 4);
-                float2* s = sum + q * (K::EPV / 2) + 2 * h;
-                s[0].x += v.x;
-                s[0].y += v.y;
-                s[1].x += v.z;
-                s[1].y += v.w;
-            }
-        }
-    }
-    store_vecs<K, K::VPL, K::LPN>(p, r, sum, lc);
 }
 
 // Row end, stored without divergent branches: every lane of the warp runs
@@ -352,10 +256,9 @@ __device__ __forceinline__ uint32_t group_or(uint32_t m, int g) {
 //
 // A row that begins in an earlier sub-chunk ends here as a tail piece, and a
 // row that goes on in a later one leaves a head piece: both go to workspace
-// slots.  DEFER: the slots are summed into C afterwards by split_row_fixup
-// (no atomics in the walk); otherwise the last piece to arrive sums them
-// (piece_row).  `wbase` is the warp's staging region.
-template <class K, bool DEFER>
+// slots, which split_row_fixup sums into C after the launch (no atomics in
+// the walk).  `wbase` is the warp's staging region.
+template <class K>
 __device__ __forceinline__ void walk_unit(const Problem& p, int i, int j, int cs,
                                           const LaneCols<K::VPL>& lc, int lane, uint32_t wbase) {
     constexpr int LPN = K::LPN, MB = K::MB, IPL = K::IPL, SS = K::SS, SPB = K::SPB;
@@ -363,8 +266,6 @@ __device__ __forceinline__ void walk_unit(const Problem& p, int i, int j, int cs
     constexpr uint32_t kStage = SS * VPL * 32 * 16;   // bytes of one stage buffer
     const int g = lane / LPN;
     const int tq = lane - g * LPN;
-    const int leader = g * LPN;
-    const unsigned gmask = LPN == 32 ? kFull : (low_bits<LPN>() << leader);
 
     int gc = 0, x0 = 0, y0 = 0, x1 = 0, y1 = 0, row_hi = 0;
     if (cs >= 0) {
@@ -545,13 +446,7 @@ __device__ __forceinline__ void walk_unit(const Problem& p, int i, int j, int cs
             decode(q[K::DEPTH - 1]);
         }
     }
-    if constexpr (DEFER) {
-        if (head) store_slot<K>(p, 2 * (int64_t)gc + 1, acc, lc);
-    } else {
-        if (tail_row >= 0)
-            piece_row<K>(p, i, j, gc, tail_row, true, nullptr, lc, tq, gmask, leader);
-        if (head) piece_row<K>(p, i, j, gc, x1, false, acc, lc, tq, gmask, leader);
-    }
+    if (head) store_slot<K>(p, 2 * (int64_t)gc + 1, acc, lc);
 }
 
 // The warp's staging region (stage_bytes per warp, after 16 reserved bytes per
@@ -575,7 +470,7 @@ spmm_csr_persistent(const Problem p, int flags) {
     const uint32_t wbase = warp_staging<K>();
     persistent_schedule<K::G>(p, flags, [&](int i, int j, int cs) {
         const LaneCols<K::VPL> lc = lane_cols<K, K::VPL, K::LPN>(p, j, lane % K::LPN);
-        walk_unit<K, true>(p, i, j, cs, lc, lane, wbase);
+        walk_unit<K>(p, i, j, cs, lc, lane, wbase);
         return true;
     });
 }
