@@ -20,10 +20,11 @@ int plan_view(spmm_plan plan, int64_t M, int64_t K, int64_t nnz, int64_t N, int3
 // split-row list (chunk capacity + TR).  Enqueued on `s` after the product.
 cudaError_t launch_split_row_fixup(const Problem& p, int64_t max_rows, cudaStream_t s);
 // The same for the `count` products of a batch table (device array), whose
-// slots lie in the batch workspace `ws`.  Enqueued on `s` after the products.
+// slots lie in the batch workspace `ws`; `max_items` bounds any product's
+// (split row, 16-byte vector) pairs.  Enqueued on `s` after the products.
 struct BatchEntry;
 cudaError_t launch_split_row_fixup_batched(const BatchEntry* table, int count, char* ws,
-                                           cudaStream_t s);
+                                           int64_t max_items, cudaStream_t s);
 // Shape of a plan (any output may be null).
 int plan_shape(spmm_plan plan, int64_t* M, int64_t* K, int64_t* nnz, int64_t* N, int32_t* TR,
                int32_t* TC);

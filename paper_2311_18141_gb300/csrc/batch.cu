@@ -50,6 +50,7 @@ struct spmm_batch_s {
     size_t ws_needed = 0;                // for the current shapes
     size_t ws_bound = 0;                 // for any shapes the autotuner may pick
     int64_t max_items = 0;               // upper bound of work items
+    int64_t fixup_items = 0;             // bound of any product's (split row, vector) pairs
     // device table order: products grouped by lane shape (one persistent launch
     // per group), each group in execution order; exec[k] = index into probs
     std::vector<int32_t> exec;
@@ -96,6 +97,7 @@ int batch_build(spmm_batch b, cudaStream_t s) {
     std::vector<size_t> plan_off(n);
     std::vector<int64_t> piece_off(n), slot_off(n);
     b->max_items = 0;
+    b->fixup_items = 0;
     for (int q = 0; q < n; ++q) {
         const spmm_problem& P = b->probs[q];
         b->lpn[q] = shape_lpn(P.N, b->TC[q], b->b_dtype);
@@ -110,6 +112,9 @@ int batch_build(spmm_batch b, cudaStream_t s) {
         const int32_t tr_any = std::max<int32_t>(b->TR[q], 16);
         ws_bound += problem_scratch(P, problem_cap(P, tr_any, kBatchMinChunk), kBatchMaxTC);
         b->max_items += b->cap[q] * b->TC[q];
+        // a product lists at most one split row per plan boundary
+        b->fixup_items =
+            std::max<int64_t>(b->fixup_items, (b->cap[q] + b->TR[q]) * (int64_t)(P.N / 4));
     }
     b->ws_needed = ws;
     b->ws_bound = std::max(ws_bound, ws);
@@ -321,7 +326,8 @@ static int batch_enqueue(spmm_batch b, void* workspace, size_t bytes, cudaStream
         if (e != cudaSuccess) return SPMM_ERR_CUDA;
     }
     // the rows that chunk boundaries cut, summed from their slots
-    if (launch_split_row_fixup_batched(b->d_table, (int)b->count, ws, s) != cudaSuccess)
+    if (launch_split_row_fixup_batched(b->d_table, (int)b->count, ws, b->fixup_items, s) !=
+        cudaSuccess)
         return SPMM_ERR_CUDA;
     return SPMM_OK;
 }

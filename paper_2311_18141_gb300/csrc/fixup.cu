@@ -82,23 +82,21 @@ __global__ void __launch_bounds__(kFixupThreads) split_row_fixup_kernel(const Pr
     }
 }
 
-// The products of a batch: block b takes products b, b + gridDim.x, ...; the
-// threads of a block share out the (split row, vector) pairs of its product.
-// A product's slots lie at ws + slot_off.
+// The products of a batch: blockIdx.y is the product, and the gridDim.x
+// blocks of a product share out its (split row, vector) pairs.  A product's
+// slots lie at ws + slot_off.
 __global__ void __launch_bounds__(kFixupThreads)
-split_row_fixup_batched_kernel(const BatchEntry* __restrict__ table, int count, char* ws) {
-    for (int q = blockIdx.x; q < count; q += gridDim.x) {
-        const BatchEntry& e = table[q];
-        const Problem& p = e.p;
-        const int n = *p.n_split;
-        if (n == 0) continue;
-        const int V4 = p.N / 4;
-        const int64_t items = (int64_t)n * V4;
-        const float* slots = reinterpret_cast<const float*>(ws + e.slot_off);
-        for (int64_t w = threadIdx.x; w < items; w += blockDim.x) {
-            const int k = (int)(w / V4);
-            fixup_row_vector(p, slots, k, (int)(w - (int64_t)k * V4));
-        }
+split_row_fixup_batched_kernel(const BatchEntry* __restrict__ table, char* ws) {
+    const BatchEntry& e = table[blockIdx.y];
+    const Problem& p = e.p;
+    const int n = *p.n_split;
+    const int V4 = p.N / 4;
+    const int64_t items = (int64_t)n * V4;
+    const float* slots = reinterpret_cast<const float*>(ws + e.slot_off);
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < items;
+         w += (int64_t)gridDim.x * blockDim.x) {
+        const int k = (int)(w / V4);
+        fixup_row_vector(p, slots, k, (int)(w - (int64_t)k * V4));
     }
 }
 
@@ -115,11 +113,20 @@ cudaError_t launch_split_row_fixup(const Problem& p, int64_t max_rows, cudaStrea
 }
 
 cudaError_t launch_split_row_fixup_batched(const BatchEntry* table, int count, char* ws,
-                                           cudaStream_t s) {
-    if (count <= 0) return cudaSuccess;
-    const int blocks = count < 1024 ? count : 1024;
-    split_row_fixup_batched_kernel<<<blocks, kFixupThreads, 0, s>>>(table, count, ws);
-    return cudaGetLastError();
+                                           int64_t max_items, cudaStream_t s) {
+    if (count <= 0 || max_items <= 0) return cudaSuccess;
+    // enough blocks per product for its largest possible list, at most 64
+    int64_t bx = (max_items + kFixupThreads - 1) / kFixupThreads;
+    if (bx > 64) bx = 64;
+    // gridDim.y holds at most 65535 products per launch
+    for (int q0 = 0; q0 < count; q0 += 65535) {
+        const int nq = count - q0 < 65535 ? count - q0 : 65535;
+        split_row_fixup_batched_kernel<<<dim3((unsigned)bx, (unsigned)nq), kFixupThreads, 0, s>>>(
+            table + q0, ws);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace spmm
