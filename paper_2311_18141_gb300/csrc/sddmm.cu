@@ -15,6 +15,10 @@
 #include "plan.cuh"
 #include "spmm_kernel.cuh"
 
+#ifndef SPMM_SDDMM_UNROLL
+#define SPMM_SDDMM_UNROLL 0   // stages per iteration of the walk loop (0: the stages of a batch)
+#endif
+
 namespace spmm {
 
 struct SddmmProblem {
@@ -165,11 +169,11 @@ __device__ __forceinline__ void sddmm_walk(const SddmmProblem& sp, int i, int cs
                 cc = __shfl_sync(kFull, X.col[0], tt, LPN);
             }
             const bool live = (X.nz >> tt) & 1u;
-            const int ok = live ? 16 : 0;
             const char* rp = brow(lc, cc);
 #pragma unroll
             for (int q = 0; q < VPL; ++q)
-                cp_async16(buf + (uint32_t)((s * S::SLOTS + q) * 512), rp + lc.qoff[q], ok);
+                cp_async16_if_set(buf + (uint32_t)((s * S::SLOTS + q) * 512), rp + lc.qoff[q], X.nz,
+                                  1u << tt);
             if (S::ROW_DC ? ((X.rs >> tt) & 1u) : live) {
                 // (first) nonzero of its row: stage the row's dC segment
                 const int row = X.rbase + __popc(X.ends & ((1u << tt) - 1u));
@@ -193,7 +197,8 @@ __device__ __forceinline__ void sddmm_walk(const SddmmProblem& sp, int i, int cs
 
     // per-lane partial dot product of item s of the stage
     auto partial = [&](uint32_t buf, int s) -> float {
-        float a = 0.0f, b = 0.0f;
+        // two FMA chains, over even and odd elements, as one packed pair
+        float2 ab = make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int q = 0; q < VPL; ++q) {
             const uint4 bv = lds128(buf + (uint32_t)((s * S::SLOTS + q) * 512));
@@ -211,13 +216,13 @@ __device__ __forceinline__ void sddmm_walk(const SddmmProblem& sp, int i, int cs
                 const uint4 dv =
                     S::ROW_DC ? dcur[q * DV + k]
                               : lds128(buf + (uint32_t)((s * S::SLOTS + VPL + q * DV + k) * 512));
-                a = fmaf(__uint_as_float(dv.x), bf[4 * k + 0], a);
-                b = fmaf(__uint_as_float(dv.y), bf[4 * k + 1], b);
-                a = fmaf(__uint_as_float(dv.z), bf[4 * k + 2], a);
-                b = fmaf(__uint_as_float(dv.w), bf[4 * k + 3], b);
+                ab = ffma2(make_float2(__uint_as_float(dv.x), __uint_as_float(dv.y)),
+                           make_float2(bf[4 * k + 0], bf[4 * k + 1]), ab);
+                ab = ffma2(make_float2(__uint_as_float(dv.z), __uint_as_float(dv.w)),
+                           make_float2(bf[4 * k + 2], bf[4 * k + 3]), ab);
             }
         }
-        return a + b;
+        return ab.x + ab.y;
     };
 
     auto consume = [&](int t, const Batch& X, int h) {
@@ -275,7 +280,10 @@ __device__ __forceinline__ void sddmm_walk(const SddmmProblem& sp, int i, int cs
     decode(B);
     decode(C);
     if (nst > 0) issue(0, A, 0);
-#pragma unroll 1
+    // unrolled by the stages of a batch, the stage's place in its batch is a
+    // constant in each copy of the body
+    constexpr int kUnroll = SPMM_SDDMM_UNROLL > 0 ? SPMM_SDDMM_UNROLL : SPB;
+#pragma unroll kUnroll
     for (int t = 0; t < nst; ++t) {
         const int h = SPB == 1 ? 0 : (t & (SPB - 1));
         if (t + 1 < nst) {
