@@ -128,3 +128,37 @@ def test_autotune_cache_round_trip(tmp_path):
     assert binding.spmm_get_device_status(ws) == 0
     check(probs, host, "batch with cached shapes")
     again.close()
+
+
+def test_batch_heavy_rows_cut_into_many_pieces():
+    """Products each holding rows of thousands of nonzeros, which the plan cuts
+    across dozens of chunks: the batched split-row sum adds more pieces per row
+    than it has slot loads in flight, for several products of one launch, with
+    beta = 1 on a random C."""
+    rng = np.random.default_rng(74)
+    probs, host = [], []
+    for k, (M, K, N, heavy) in enumerate([(700, 8000, 16, 6000), (1500, 9000, 64, 8000),
+                                          (900, 4000, 64, 3500), (400, 12000, 16, 11000)]):
+        lens = rng.integers(0, 30, M)
+        lens[rng.integers(0, M, 3)] = heavy        # three heavy rows per product
+        lens[0] = 0
+        lens[-1] = 5
+        rowptr = np.zeros(M + 1, np.int64)
+        rowptr[1:] = np.cumsum(lens)
+        colind = np.concatenate([np.sort(rng.choice(K, int(l), replace=False)) for l in lens if l])
+        vals = torch.from_numpy(rng.uniform(-1, 1, colind.size).astype(np.float32)).to(torch.bfloat16)
+        B = inputs.dense_normal(K, N, seed=80 + k, device="cuda").to(torch.bfloat16)
+        C0 = inputs.dense_normal(M, N, seed=90 + k, device="cuda")
+        rp = torch.from_numpy(rowptr.astype(np.int32)).cuda()
+        ci = torch.from_numpy(colind.astype(np.int32)).cuda()
+        probs.append(dict(rowptr=rp, colind=ci, vals=vals.cuda(), B=B, C=C0.clone(), M=M, K=K, N=N,
+                          beta=1.0))
+        A = inputs.CSR(rp, ci, vals.float().cuda(), M, K)
+        host.append((A, vals, B, C0.clone()))
+    batch = binding.Batch(probs)
+    ws = binding.workspace(batch.workspace_bytes)
+    batch.run(ws)
+    torch.cuda.synchronize()
+    assert binding.spmm_get_device_status(ws) == 0
+    check(probs, host, "batched heavy rows")
+    batch.close()
