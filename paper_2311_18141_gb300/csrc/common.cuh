@@ -76,19 +76,12 @@ __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory");
 }
 
-// ---- mbarriers and bulk asynchronous copies (the TMA engine) ----
-// A bulk copy moves `bytes` (a multiple of 16, both addresses 16-byte
-// aligned) from global to shared memory and reports completion as bytes on
-// an mbarrier; the thread that expects them arms the barrier once per phase.
+// ---- mbarriers, waited on with a bound ----
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(bar), "r"(count) : "memory");
 }
 __device__ __forceinline__ void mbar_init_fence() {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                 :: "r"(bar), "r"(bytes) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
     uint32_t ok;
@@ -106,17 +99,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
     while (!mbar_try_wait(bar, parity))
         if (clock64() - t0 > (1ll << 31)) return false;
     return true;
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
-                                         uint32_t bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes"
-                 " [%0], [%1], %2, [%3];"
-                 :: "r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
-}
-// Orders this thread's earlier generic-proxy shared-memory accesses before
-// its later async-proxy (bulk copy) accesses.
-__device__ __forceinline__ void fence_proxy_async_smem() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 __device__ __forceinline__ uint4 lds128(uint32_t smem_addr) {
@@ -293,16 +275,6 @@ template <> __device__ __forceinline__ float aval<TagE4M3, false>(const void* v,
     return e4m3x2_to_f2((uint16_t)__ldg(reinterpret_cast<const unsigned char*>(v) + e)).x;
 }
 
-// Position of the q-th (0-based) set bit of m; requires q < popc(m).  Binary
-// search on prefix popcounts; the result is always in [0, 31].
-__device__ __forceinline__ int nth_set_bit(unsigned m, int q) {
-    int pos = 0;
-    const int need = q + 1;
-#pragma unroll
-    for (int w = 16; w >= 1; w >>= 1)
-        if (__popc(m & ((1u << (pos + w)) - 1u)) < need) pos += w;
-    return pos;
-}
 
 // ----------------------------------------------------------- arguments ----
 

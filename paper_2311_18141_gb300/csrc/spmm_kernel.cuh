@@ -97,10 +97,10 @@ struct KCfg {
     static_assert(SPB == 1 || IPL == 1, "split batches need one item per lane");
 };
 
-// Dynamic shared memory of a persistent CTA of `warps` warps: a pair of
-// mbarriers (16 bytes) per warp, then the warps' staging regions.
+// Dynamic shared memory of a persistent CTA of `warps` warps: the warps'
+// staging regions, one after the other.
 __host__ __device__ constexpr int smem_bytes(int warps, int stage_bytes) {
-    return warps * (16 + stage_bytes);
+    return warps * stage_bytes;
 }
 
 // Dynamic shared memory of the persistent kernels (staging buffers).
@@ -449,14 +449,13 @@ __device__ __forceinline__ void walk_unit(const Problem& p, int i, int j, int cs
     if (head) store_slot<K>(p, 2 * (int64_t)gc + 1, acc, lc);
 }
 
-// The warp's staging region (stage_bytes per warp, after 16 reserved bytes per
-// warp at the start of the CTA's dynamic shared memory).
+// The warp's staging region (stage_bytes per warp, in warp order from the
+// start of the CTA's dynamic shared memory).
 template <class K>
 __device__ __forceinline__ uint32_t warp_staging(int stage_bytes = K::STAGE_BYTES) {
-    const int warps = blockDim.x >> 5;
     const int w = threadIdx.x >> 5;
     const uint32_t smem = (uint32_t)__cvta_generic_to_shared(spmm_dyn_smem);
-    return smem + (uint32_t)(warps * 16 + w * stage_bytes);
+    return smem + (uint32_t)(w * stage_bytes);
 }
 
 // The persistent kernel: each warp is an independent worker (see
