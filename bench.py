@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--lanes", type=int, default=0,
                     help="spmm_tuning.lanes_per_item: 0 default, 2 or 4 lanes per column "
                          "block of 4 or 8 vectors")
-    ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--e2e-steps", type=int, default=12)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
@@ -441,15 +441,16 @@ def run_ours(args):
     # end-to-end through the C ABI's host-buffer pipeline (spmm_host_pipe_*):
     # every step copies A and B from pinned host memory to the device,
     # multiplies, and copies C back into host memory, all inside the timed
-    # region.  depth 1 runs the steps one after the other; depth 2 overlaps the
-    # upload of step k+1 and the download of step k-1 with step k's product.
+    # region.  depth 1 runs the steps one after the other; depth d keeps d
+    # device slots, so the uploads of the next steps and the downloads of the
+    # previous ones overlap the current step's product.
     e2e = None
     if rank == 0 or world > 1:
         rp_h = A.rowptr.cpu().pin_memory()
         ci_h = A.colind.cpu().pin_memory()
         v_h = A.vals.cpu().pin_memory()
         B_h = B.cpu().pin_memory()
-        C_hs = [torch.empty(M, N).pin_memory() for _ in range(2)]
+        C_hs = [torch.empty(M, N).pin_memory() for _ in range(3)]
         h2d = sum(t.numel() * t.element_size() for t in (rp_h, ci_h, v_h, B_h))
         d2h = C_hs[0].numel() * C_hs[0].element_size()
         assert binding.spmm_get_device_status(ws) == 0
@@ -463,25 +464,27 @@ def run_ours(args):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             for k in range(n_e2e):
-                pipe.submit(rp_h, ci_h, v_h, B_h, C_hs[k % 2])
+                pipe.submit(rp_h, ci_h, v_h, B_h, C_hs[k % len(C_hs)])
             pipe.wait()
             ms = (time.perf_counter() - t0) * 1e3 / n_e2e
             pipe.close()
             return ms
 
-        serial_ms = pipe_ms(1)
-        e2e_ms = pipe_ms(2)
+        depths = (1, 2, 3)
+        by_depth = [pipe_ms(d) for d in depths]
         if world > 1:   # the job's step time is the slowest rank's
-            t = torch.tensor([serial_ms, e2e_ms], dtype=torch.float64, device=dev)
+            t = torch.tensor(by_depth, dtype=torch.float64, device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            serial_ms, e2e_ms = float(t[0]), float(t[1])
-        # both depths are the same public call; whether the two copy directions
-        # really overlap varies from box to box, so the faster depth is reported
-        depth, best_ms = (2, e2e_ms) if e2e_ms <= serial_ms else (1, serial_ms)
+            by_depth = [float(x) for x in t]
+        # every depth is the same public call; how well the copies of
+        # consecutive steps overlap on the host link varies from machine to
+        # machine, so the pipeline depth is chosen by timing, like a tuning knob
+        k_best = min(range(len(depths)), key=lambda k: by_depth[k])
+        depth, best_ms = depths[k_best], by_depth[k_best]
         e2e = {"value": flops * world / (best_ms * 1e-3) / 1e9, "unit": "GFLOP/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": best_ms,
                "steps": n_e2e, "pipelined": depth > 1, "api": f"spmm_host_pipe (depth {depth})",
-               "ms_per_step_by_depth": {"1": serial_ms, "2": e2e_ms}}
+               "ms_per_step_by_depth": {str(d): ms for d, ms in zip(depths, by_depth)}}
         del rp_h, ci_h, v_h, B_h, C_hs
 
     # optional context: the paper's own local kernel, cuSPARSE SpMM (through
