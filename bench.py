@@ -52,7 +52,8 @@ def parse():
     ap.add_argument("--n", type=int, default=128)
     ap.add_argument("--grid", default="16x4")
     ap.add_argument("--chunk", type=int, default=0)
-    ap.add_argument("--warps", type=int, default=0)
+    ap.add_argument("--warps", type=int, default=0,
+                    help="spmm_tuning.warps_per_cta: 0 library default (7 or 8), 1 to 8")
     ap.add_argument("--order", type=int, default=16,
                     help="spmm_tuning.tile_order (16: one queue per tile row, chunks of its "
                          "tiles handed out in turn)")
@@ -514,8 +515,8 @@ def run_ours(args):
         del B
         torch.cuda.empty_cache()
         precision = precision_results(A, dev, args.grid, max(5, min(args.steps, 20)),
-                                      max(3, args.warmup))
-        small = small_results(dev)
+                                      max(3, args.warmup), warps=args.warps)
+        small = small_results(dev, warps=args.warps)
         B = None
 
     cpu = None
@@ -604,7 +605,7 @@ def sub_problem(rp, ci, rows):
     return sub_rp, local.astype(np.int32), pos, cols
 
 
-def precision_results(A, dev, grid: str, steps: int, warmup: int):
+def precision_results(A, dev, grid: str, steps: int, warmup: int, warps: int = 0):
     """The precision form at full size: FP16 A values; B of width 256 stored as
     FP32, BF16 and E4M3 with per-row FP32 scales; FP32 accumulation.  For each
     format: the time of one spmm_csr (CUDA events, mean over `steps` after
@@ -631,7 +632,8 @@ def precision_results(A, dev, grid: str, steps: int, warmup: int):
     ref0 = oracle.spmm(sub_rp, sub_ci, v, b32)
     bound0 = oracle.abs_bound(sub_rp, sub_ci, v, b32)
     out = {}
-    plan = binding.Plan(A.rowptr, M, K, nnz, N, TR, TC)
+    plan = binding.Plan(A.rowptr, M, K, nnz, N, TR, TC,
+                        tuning=binding.make_tuning(warps_per_cta=warps))
     ws = binding.workspace(plan.workspace_bytes, dev)
     C = torch.empty(M, N, device=dev)
     for fmt in ("f32", "bf16", "e4m3"):
@@ -681,7 +683,7 @@ def precision_results(A, dev, grid: str, steps: int, warmup: int):
             "e4m3_faster_than_bf16": out["e4m3"]["ms"] < out["bf16"]["ms"]}
 
 
-def small_results(dev, steps: int = 200):
+def small_results(dev, steps: int = 200, warps: int = 0):
     """The small FP32 form: A 4096 x 4096 with exactly 16 nonzeros per row, B
     4096 x 32.  L2-resident and launch-bound, so times are per call: the
     device time of back-to-back calls (CUDA events), the host time of the
@@ -694,7 +696,8 @@ def small_results(dev, steps: int = 200):
     N = 32
     B = inputs.dense_normal(4096, N, seed=1, device=dev)
     C = torch.empty(4096, N, device=dev)
-    plan = binding.Plan(A.rowptr, A.M, A.K, A.nnz, N, 1, 1)
+    plan = binding.Plan(A.rowptr, A.M, A.K, A.nnz, N, 1, 1,
+                        tuning=binding.make_tuning(warps_per_cta=warps))
     ws = binding.workspace(plan.workspace_bytes, dev)
     stream = torch.cuda.current_stream()
 
@@ -741,7 +744,7 @@ def run_precision(args):
     dev = torch.device("cuda")
     binding.load_library()
     A, _ = make_workload(args.scale, 8, dev)
-    print(json.dumps(precision_results(A, dev, args.grid, args.steps, args.warmup)), flush=True)
+    print(json.dumps(precision_results(A, dev, args.grid, args.steps, args.warmup, warps=args.warps)), flush=True)
 
 
 def run_gcn(args):

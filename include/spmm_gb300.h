@@ -72,7 +72,7 @@ typedef struct spmm_plan_s* spmm_plan;
 typedef struct spmm_tuning {
     int32_t chunk_items;   /* merge-path items (rows + nonzeros) per plan chunk; a
                               warp's work unit is 32/LPN chunks, one per lane group     */
-    int32_t warps_per_cta; /* 4 or 8                                                  */
+    int32_t warps_per_cta; /* 1 to 8; 0 = 7 where four 7-warp CTAs fit on an SM, else 8 */
     int32_t ctas_per_sm;   /* persistent CTAs per SM; 0 = as many as fit              */
     int32_t tile_order;    /* bit 0: steal along the tile column first (else the row);
                               bit 1: stagger home tiles per warp (else per CTA);

@@ -72,7 +72,7 @@ static Scratch scratch_layout(int32_t TR, int32_t TC, int64_t cap, int64_t N) {
 void resolve_tuning(const spmm_tuning* in, spmm_tuning* out) {
     memset(out, 0, sizeof(*out));
     if (in) *out = *in;
-    if (out->warps_per_cta != 4 && out->warps_per_cta != 8) out->warps_per_cta = 8;
+    if (out->warps_per_cta < 0 || out->warps_per_cta > 8) out->warps_per_cta = 0;
     if (out->ctas_per_sm < 0) out->ctas_per_sm = 0;
     if (out->tile_order < 0 || out->tile_order > 31) out->tile_order = 0;
     if (out->chunk_items < 0) out->chunk_items = 0;

@@ -85,7 +85,7 @@ template <int LPN>
 cudaError_t launch_gather(const char* B, uint32_t ldb_bytes, uint32_t seg_bytes,
                           const int32_t* colind, int nnz, int TC, int S, float* out,
                           int ctas_per_sm, cudaStream_t s) {
-    static std::atomic<int> cache[kMaxDevices][3];
+    static std::atomic<int> cache[kMaxDevices][kOccSlots];
     auto kern = gather_bench_kernel<LPN>;
     const int per_sm = cached_ctas_per_sm(kern, 256, 0, cache);
     if (per_sm == 0) return cudaErrorInvalidValue;

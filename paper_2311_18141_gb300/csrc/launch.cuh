@@ -8,7 +8,7 @@
 namespace spmm {
 
 struct LaunchOpts {
-    int warps_per_cta;   // 4 or 8
+    int warps_per_cta;   // 1 to 8; 0 = chosen by the launcher
     int ctas_per_sm;     // 0 = occupancy limit
     int flags;           // kFlagOrderColumn | kFlagWarpHome
     int64_t units;       // work units (upper bound), caps the grid
@@ -42,17 +42,19 @@ using BatchLaunchFn = cudaError_t (*)(int lpn, const BatchEntry* table, const in
 // device raises the kernel's dynamic shared-memory limit to the device's
 // opt-in maximum less its static shared memory, so every later launch shape
 // fits under it.  0 on a CUDA
-// error.  cache[dev][0] holds 128-thread CTAs, [1] 256-thread ones, [2] is 1
+// error.  cache[dev][w - 1] holds CTAs of w warps (1 to 8), cache[dev][8] is 1
 // once the attribute is set.
+constexpr int kOccSlots = 9;
 template <class Kern>
 int cached_ctas_per_sm(Kern kern, int threads, size_t smem,
-                       std::atomic<int> (&cache)[kMaxDevices][3]) {
+                       std::atomic<int> (&cache)[kMaxDevices][kOccSlots]) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 0;
-    const int slot = threads > 128 ? 1 : 0;
+    if (threads < 32 || threads > 256 || threads % 32 != 0) return 0;
+    const int slot = threads / 32 - 1;
     int per_sm = cache[dev][slot].load(std::memory_order_relaxed);
     if (per_sm > 0) return per_sm;
-    if (cache[dev][2].load(std::memory_order_acquire) == 0) {
+    if (cache[dev][kOccSlots - 1].load(std::memory_order_acquire) == 0) {
         int optin = 0;
         if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
             cudaSuccess)
@@ -68,13 +70,34 @@ int cached_ctas_per_sm(Kern kern, int threads, size_t smem,
             return 0;
         if (smem == 0)   // no shared memory: give the SM's whole L1/shared array to L1
             cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
-        cache[dev][2].store(1, std::memory_order_release);
+        cache[dev][kOccSlots - 1].store(1, std::memory_order_release);
     }
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess)
         return 0;
     if (per_sm < 1) per_sm = 1;
     cache[dev][slot].store(per_sm, std::memory_order_relaxed);
     return per_sm;
+}
+
+// CTA size of a persistent launch whose tuning leaves it open (0): 7 warps
+// when four such CTAs fit on an SM (28 resident warps, the register file and
+// the 228 KB of shared memory both just enough at 72 registers and 8 KB of
+// staging per warp), else 8 warps.  Found once per device and kernel; 0 on a
+// CUDA error.
+template <class Kern>
+int auto_warps(Kern kern, size_t smem_per_warp,
+               std::atomic<int> (&cache)[kMaxDevices][kOccSlots],
+               std::atomic<int> (&pick)[kMaxDevices]) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return 0;
+    int w = pick[dev].load(std::memory_order_relaxed);
+    if (w > 0) return w;
+    const int per8 = cached_ctas_per_sm(kern, 256, 8 * smem_per_warp, cache);
+    const int per7 = cached_ctas_per_sm(kern, 224, 7 * smem_per_warp, cache);
+    if (per8 == 0 || per7 == 0) return 0;
+    w = per7 * 7 > per8 * 8 ? 7 : 8;
+    pick[dev].store(w, std::memory_order_relaxed);
+    return w;
 }
 
 // Grid of a persistent launch: SMs x resident CTAs (capped by `ctas_per_sm`

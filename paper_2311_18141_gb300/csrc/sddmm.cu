@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(256, SPMM_SDDMM_MINBLOCKS) sddmm_persistent(co
 
 template <class Tag, int LPN, int VPL>
 static cudaError_t launch_sddmm_one(const SddmmProblem& s, int64_t units, cudaStream_t st) {
-    static std::atomic<int> cache[kMaxDevices][3];
+    static std::atomic<int> cache[kMaxDevices][kOccSlots];
     using K = KCfg<TagF32, Tag, LPN, VPL>;
     auto kern = sddmm_persistent<Tag, LPN, VPL>;
     const size_t smem = (size_t)8 * SCfg<K>::STAGE_BYTES;

@@ -10,30 +10,33 @@ namespace spmm {
 
 template <class TA, class TB, int LPN, int VPL>
 cudaError_t launch_one(const Problem& p, const LaunchOpts& o, cudaStream_t s) {
-    static std::atomic<int> cache[kMaxDevices][3];
+    static std::atomic<int> cache[kMaxDevices][kOccSlots];
+    static std::atomic<int> pick[kMaxDevices];
     auto kern = spmm_csr_persistent<TA, TB, LPN, VPL>;
-    const int threads = o.warps_per_cta * 32;
-    const size_t smem = (size_t)smem_bytes(o.warps_per_cta, KCfg<TA, TB, LPN, VPL>::STAGE_BYTES);
+    constexpr int stage = KCfg<TA, TB, LPN, VPL>::STAGE_BYTES;
+    const int warps = o.warps_per_cta > 0 ? o.warps_per_cta : auto_warps(kern, stage, cache, pick);
+    if (warps == 0) return cudaErrorInvalidValue;
+    const int threads = warps * 32;
+    const size_t smem = (size_t)smem_bytes(warps, stage);
     const int per_sm = cached_ctas_per_sm(kern, threads, smem, cache);
     if (per_sm == 0) return cudaErrorInvalidValue;
     // o.units counts plan chunks; a warp's unit is G of them
     constexpr int G = KCfg<TA, TB, LPN, VPL>::G;
-    const int64_t grid = persistent_grid(per_sm, o.ctas_per_sm, (o.units + G - 1) / G,
-                                         o.warps_per_cta);
+    const int64_t grid = persistent_grid(per_sm, o.ctas_per_sm, (o.units + G - 1) / G, warps);
     kern<<<(unsigned)grid, threads, smem, s>>>(p, o.flags);
     return cudaGetLastError();
 }
 
 template <class TA, class TB, int LPN, int NV>
 cudaError_t launch_wide_one(const Problem& p, const LaunchOpts& o, cudaStream_t s) {
-    static std::atomic<int> cache[kMaxDevices][3];
+    static std::atomic<int> cache[kMaxDevices][kOccSlots];
     auto kern = spmm_csr_wide<TA, TB, LPN, NV>;
-    const int threads = o.warps_per_cta * 32;
+    const int threads = (o.warps_per_cta > 0 ? o.warps_per_cta : 8) * 32;
     const int per_sm = cached_ctas_per_sm(kern, threads, 0, cache);
     if (per_sm == 0) return cudaErrorInvalidValue;
     constexpr int G = WCfg<TA, TB, LPN, NV>::G;
     const int64_t grid = persistent_grid(per_sm, o.ctas_per_sm, (o.units + G - 1) / G,
-                                         o.warps_per_cta);
+                                         threads / 32);
     kern<<<(unsigned)grid, threads, 0, s>>>(p, o.flags);
     return cudaGetLastError();
 }
@@ -72,7 +75,7 @@ template <class TA, class TB, int LPN>
 cudaError_t launch_batched_one(const BatchEntry* table, const int64_t* item_base, int count,
                                char* ws, int* counter, int64_t max_items, int ctas_per_sm,
                                cudaStream_t s) {
-    static std::atomic<int> cache[kMaxDevices][3];
+    static std::atomic<int> cache[kMaxDevices][kOccSlots];
     auto kern = spmm_csr_batched_kernel<TA, TB, LPN>;
     const int threads = kBatchWarps * 32;
     const size_t smem = (size_t)smem_bytes(kBatchWarps, batch_stage_bytes<TA, TB, LPN>());

@@ -10,7 +10,7 @@ namespace {
 template <class TA, class TB, int LPN>
 cudaError_t launch_spec_one(const Problem& p, const LaunchOpts& o, cudaStream_t s) {
     using K = KCfg<TA, TB, LPN, 1>;
-    static std::atomic<int> cache[kMaxDevices][3];
+    static std::atomic<int> cache[kMaxDevices][kOccSlots];
     auto kern = spmm_csr_spec<TA, TB, LPN, 1>;
     constexpr int warps = 8;   // four producer/consumer pairs
     const size_t smem = (size_t)spec_smem_bytes(warps, SpecCfg<K>::SLOT_BYTES);

@@ -68,7 +68,8 @@ def test_widths(N, kernel):
                                   dict(tile_order=4), dict(plan=False),
                                   dict(warps_per_cta=4, tile_order=5), dict(tile_order=8),
                                   dict(tile_order=9), dict(tile_order=16), dict(tile_order=24),
-                                  dict(warps_per_cta=4, tile_order=16)])
+                                  dict(warps_per_cta=4, tile_order=16), dict(warps_per_cta=7),
+                                  dict(warps_per_cta=5, tile_order=16), dict(warps_per_cta=3)])
 @pytest.mark.parametrize("kernel", KERNELS)
 def test_launch_options(opts, kernel):
     A = inputs.rmat_csr(12, 8, seed=6)
