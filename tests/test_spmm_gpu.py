@@ -323,3 +323,42 @@ def test_trace_records_account_for_every_unit(tile_order, kernel):
     torch.cuda.synchronize()
     assert torch.count_nonzero(buf) == 0
     plan.close()
+
+
+@pytest.mark.parametrize("warps", [0, 5, 8])
+def test_cta_size_of_the_persistent_grid(warps):
+    """The launch fills every SM with whole CTAs of the requested size; the
+    default (0) is 7-warp CTAs, four per SM, where they fit the registers and
+    shared memory, else 8-warp CTAs, three per SM. With short chunks there are
+    more warp units than resident warps, so the grid is not cut short, and the
+    trace holds one record per launched warp."""
+    A = inputs.rmat_csr(14, 16, seed=79)
+    N, TR, TC = 128, 16, 4
+    Ad = A.to("cuda")
+    B = inputs.dense_normal(A.K, N, seed=80, device="cuda")
+    plan = binding.Plan(Ad.rowptr, A.M, A.K, A.nnz, N, TR, TC,
+                        tuning=binding.make_tuning(chunk_items=32, warps_per_cta=warps,
+                                                   tile_order=16))
+    ws = binding.workspace(plan.workspace_bytes)
+    buf = binding.trace_buffer(1 << 15)
+    plan.set_trace(buf)
+    C = torch.empty(A.M, N, device="cuda")
+    binding.spmm_csr(Ad.rowptr, Ad.colind, Ad.vals, B, C, A.M, A.K, N, A.nnz, plan=plan, ws=ws)
+    torch.cuda.synchronize()
+    assert binding.spmm_get_device_status(ws) == 0
+    rec = binding.read_trace(buf)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    chunks, _ = plan.units()
+    assert chunks * TC // 4 > sms * 32   # more warp units (4 chunks each) than warps
+    assert rec.size % sms == 0
+    per_sm = rec.size // sms
+    if warps == 0:
+        assert per_sm in (28, 24)
+    elif warps == 5:
+        assert per_sm == 25   # 5 CTAs: 5 x (40 KB of staging + 1 KB) fit 228 KB
+    else:
+        assert per_sm == 24   # 3 CTAs: a fourth 64 KB of staging does not fit
+    ref, bound = ref_and_bound(A, B.cpu())
+    assert_close_rel(C.cpu().numpy(), ref, bound, TOL_F32, f"warps={warps}")
+    plan.set_trace(None)
+    plan.close()
