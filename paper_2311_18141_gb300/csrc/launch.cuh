@@ -41,9 +41,8 @@ using BatchLaunchFn = cudaError_t (*)(int lpn, const BatchEntry* table, const in
 // and the occupancy query stay off the per-call path).  The first query on a
 // device raises the kernel's dynamic shared-memory limit to the device's
 // opt-in maximum less its static shared memory, so every later launch shape
-// fits under it.  0 on a CUDA
-// error.  cache[dev][w - 1] holds CTAs of w warps (1 to 8), cache[dev][8] is 1
-// once the attribute is set.
+// fits under it.  0 on a CUDA error.  cache[dev][w - 1] holds CTAs of w warps
+// (1 to 8), cache[dev][8] is 1 once the attribute is set.
 constexpr int kOccSlots = 9;
 template <class Kern>
 int cached_ctas_per_sm(Kern kern, int threads, size_t smem,
