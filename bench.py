@@ -38,8 +38,8 @@ WORKLOAD = "rmat-s22-ef16-n128-fp32-grid16x4"
 NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e nominal bandwidth, for the second roofline fraction
 FALLBACK_HBM_GBS = 6800.0
 PROFILE = os.path.join(ROOT, "profiles", "spmm_csr_persistent_rmat_s22_n128.md")
-KERNEL_SOURCES = ["common.cuh", "schedule.cuh", "spmm_kernel.cuh", "spmm_launch_impl.cuh",
-                  "spmm_f32_f32.cu", "plan.cu", "fixup.cu"]
+KERNEL_SOURCES = ["common.cuh", "schedule.cuh", "spmm_kernel.cuh", "launch.cuh",
+                  "spmm_launch_impl.cuh", "spmm_f32_f32.cu", "plan.cu", "fixup.cu"]
 
 
 def parse():
