@@ -398,8 +398,10 @@ def run_ours(args):
     torch.cuda.synchronize()
     assert binding.spmm_get_device_status(ws) == 0
 
+    # this rank's GPU as nvidia-smi names it: its entry of CUDA_VISIBLE_DEVICES
+    # (an index or a UUID), else its local index
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
-    gpu_id = vis[local].strip() if local < len(vis) and vis[local].strip() else None
+    gpu_id = vis[local].strip() if local < len(vis) and vis[local].strip() else str(local)
     sampler = ClockSampler(gpu_id)
     sampler.start()
     if world > 1:

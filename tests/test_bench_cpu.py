@@ -127,3 +127,20 @@ def test_trace_summary_of_hand_made_records():
     assert abs(t["units_per_warp_max_over_avg"] - 1.5) < 1e-12
     assert abs(t["stolen_share"] - 0.25) < 1e-12
     assert bench.trace_summary(rec[:0]) is None
+
+
+def test_clock_summary_of_hand_made_samples():
+    """Median SM clock under load, the maximum, and every throttle reason seen
+    Active in any sample (the fields a run is accepted or rejected on)."""
+    s = bench.ClockSampler("0")
+    row = "0, {sm}, 2070, 900.0, 0x0, {hw}, Not Active, Not Active, {pc}"
+    s.out = [row.format(sm=sm, hw=hw, pc=pc).split(",")
+             for sm, hw, pc in [(2070, "Not Active", "Not Active"),
+                                (1980, "Not Active", "Active"),
+                                (2070, "Not Active", "Not Active")]]
+    c = s.summary()
+    assert c["sm_mhz"] == 2070.0 and c["sm_max_mhz"] == 2070.0 and c["samples"] == 3
+    assert c["reasons"] == ["sw_power_cap"]
+    s.out[0][5] = " Active"
+    assert bench.ClockSampler.summary(s)["reasons"] == ["hw_slowdown", "sw_power_cap"]
+    assert bench.ClockSampler("0").summary()["reasons"] == ["no samples"]
